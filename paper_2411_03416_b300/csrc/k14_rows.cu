@@ -1,0 +1,6 @@
+// Single-row kernels (marginals, quadrature, one trial), state dimension 14.
+#include "pgvimp_kernels.cuh"
+
+namespace pgv {
+template cudaError_t launch_rows<14>(const Launch& L, int phase, double arg_d, int mixed);
+}  // namespace pgv

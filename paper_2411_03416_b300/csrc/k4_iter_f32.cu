@@ -1,0 +1,6 @@
+// Fused proximal iterations, state dimension 4, FP32 quadrature.
+#include "pgvimp_kernels.cuh"
+
+namespace pgv {
+template cudaError_t launch_iter<4, float>(const Launch& L, int iters);
+}  // namespace pgv

@@ -1,0 +1,6 @@
+// Single-row kernels (marginals, quadrature, one trial), state dimension 4.
+#include "pgvimp_kernels.cuh"
+
+namespace pgv {
+template cudaError_t launch_rows<4>(const Launch& L, int phase, double arg_d, int mixed);
+}  // namespace pgv

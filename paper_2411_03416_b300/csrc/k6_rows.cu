@@ -1,0 +1,6 @@
+// Single-row kernels (marginals, quadrature, one trial), state dimension 6.
+#include "pgvimp_kernels.cuh"
+
+namespace pgv {
+template cudaError_t launch_rows<6>(const Launch& L, int phase, double arg_d, int mixed);
+}  // namespace pgv

@@ -1,0 +1,171 @@
+"""End-to-end parity of whole plans (Alg. 1, Alg. 2) on the GPU against the
+oracle, on the configurations' full sizes and on small / edge cases, in the
+launch configuration the benchmark uses (one batch, one thread per plan)."""
+from dataclasses import replace
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+from _parity import TOL_FP64_DENSE, TOL_FP64_SMALL, TOL_MIXED, compare_plan, gpu_solve, rel_mu, rel_sigma
+
+pytestmark = pytest.mark.gpu
+
+MIXED, FP64 = 1, 0
+
+
+@pytest.fixture(scope="module")
+def pg():
+    import torch
+    assert torch.cuda.is_available(), "these tests need a CUDA device"
+    import paper_2411_03416_b300 as pg
+    pg.lib()
+    return pg
+
+
+@pytest.mark.parametrize("prec,tol", [(FP64, TOL_FP64_SMALL), (MIXED, TOL_MIXED)])
+def test_c1_point2d(pg, prec, tol):
+    pb, op = W.c1_point2d()
+    res = gpu_solve([pb], [op], prec)[0]
+    info, ora = compare_plan(pb, op, res, rtol_mu=tol["mu"], rtol_sigma=tol["sigma"])
+    assert len(res.logs) == op.iters
+    # logged costs follow the oracle's
+    for lg, lo in zip(res.logs, ora.logs):
+        assert abs(lg["collision_cost"] - lo["collision_cost"]) <= 1e-3 * max(1.0, abs(lo["collision_cost"]))
+        assert abs(lg["entropy"] - lo["entropy"]) <= 1e-6 * abs(lo["entropy"])
+
+
+# At N = 750 the iteration is chaotic in FP64: the oracle against itself with a
+# 1e-12 relative change of the goal (same step sequence) differs by 1.7e-7
+# after one iteration, 5e-7 after three, 7e-2 after six and 0.27 after thirty.
+# Whole-plan agreement is therefore bounded by that divergence; the full-size
+# parity runs the first iterations, and the whole plan is checked through
+# properties that hold at any size.
+@pytest.mark.parametrize("iters", [1, 3])
+@pytest.mark.parametrize("prec,tol", [(FP64, dict(mu=1e-5, sigma=1e-5)), (MIXED, TOL_MIXED)])
+def test_c2_dense_horizon_full_size_first_iterations(pg, prec, tol, iters):
+    pb, op = W.c2_point2d_dense(iters=iters)
+    res = gpu_solve([pb], [op], prec)[0]
+    compare_plan(pb, op, res, rtol_mu=tol["mu"], rtol_sigma=tol["sigma"])
+
+
+def _check_plan_invariants(pb, op, res):
+    assert np.all(np.isfinite(res.mu)) and np.all(np.isfinite(res.Sd))
+    for S in res.Sd:
+        np.linalg.cholesky(0.5 * (S + S.T))           # every marginal covariance is SPD
+    for l in res.logs:
+        assert l["trials"] >= 1
+        if l["beta"] > 0:
+            assert l["kl"] <= op.kl_eps * (1 + 1e-12)   # accepted steps respect the KL bound
+            k = l["beta"] / op.beta_max * 2 ** op.max_bisect
+            assert abs(k - round(k)) < 1e-9            # steps are dyadic fractions of beta_max
+
+
+@pytest.mark.parametrize("prec", [FP64, MIXED])
+def test_c2_dense_horizon_full_plan_invariants(pg, prec):
+    pb, op = W.c2_point2d_dense()
+    res = gpu_solve([pb], [op], prec)[0]
+    assert len(res.logs) == op.iters
+    _check_plan_invariants(pb, op, res)
+    # the plan moves the trajectory off the obstacles: collision cost falls
+    assert res.logs[-1]["collision_cost"] < res.logs[0]["collision_cost"]
+
+
+@pytest.mark.parametrize("prec,tol", [(FP64, TOL_FP64_SMALL), (MIXED, TOL_MIXED)])
+def test_c3_arm_short(pg, prec, tol):
+    pb, op = W.c3_arm(N=30, iters=10)
+    res = gpu_solve([pb], [op], prec)[0]
+    compare_plan(pb, op, res, rtol_mu=tol["mu"], rtol_sigma=tol["sigma"])
+
+
+def test_c3_arm_full_size(pg):
+    pb, op = W.c3_arm()
+    res = gpu_solve([pb], [op], MIXED)[0]
+    compare_plan(pb, op, res, rtol_mu=TOL_MIXED["mu"], rtol_sigma=TOL_MIXED["sigma"])
+
+
+# Alg. 2 on the quadrotor is chaotic as well: at N = 40 (3 x 5 iterations) the
+# oracle against itself moves by 3e-9 (mean) / 6e-8 (covariances) for a 1e-12
+# change of the goal and by 4e-2 / 4e-1 for a 1e-7 change (the size of FP32
+# quadrature error in the linearisation); at N = 300 a 1e-12 change ends 36%
+# away.  FP64 runs are compared over the whole short plan with a bound 10x the
+# measured FP64 divergence; the FP32-quadrature path over its first
+# linearisation and iterations.
+def test_c4_quadrotor_slr_short_fp64(pg):
+    pb, op = W.c4_quadrotor(N=40, iters=5, slr_iters=3)
+    res = gpu_solve([pb], [op], FP64)[0]
+    compare_plan(pb, op, res, rtol_mu=3e-8, rtol_sigma=1e-6)
+    assert len(res.logs) == 15
+
+
+@pytest.mark.parametrize("N,iters", [(40, 2), (300, 2)])
+def test_c4_quadrotor_first_linearisation_mixed(pg, N, iters):
+    pb, op = W.c4_quadrotor(N=N, iters=iters, slr_iters=1)
+    res = gpu_solve([pb], [op], MIXED)[0]
+    compare_plan(pb, op, res, rtol_mu=TOL_MIXED["mu"], rtol_sigma=TOL_MIXED["sigma"])
+
+
+@pytest.mark.parametrize("prec", [FP64, MIXED])
+def test_c4_quadrotor_full_plan_invariants(pg, prec):
+    pb, op = W.c4_quadrotor()
+    res = gpu_solve([pb], [op], prec)[0]
+    assert len(res.logs) == op.iters * op.slr_iters
+    _check_plan_invariants(pb, op, res)
+
+
+# ------------------------------------------------------------------ edge cases
+
+def test_minimal_horizon_and_no_obstacles_fixed_point(pg):
+    """N = 1; and psi = 0 with an unbounded KL: the iteration contracts to the
+    GP prior (posterior given start and goal) at rate 1/(beta+1)."""
+    pb, op = W.c1_point2d(N=1, iters=3)
+    res = gpu_solve([pb], [op], FP64)[0]
+    compare_plan(pb, op, res, rtol_mu=1e-10, rtol_sigma=1e-10)
+    pb, op = W.c1_point2d(N=25)
+    pb = replace(pb, cost_kind=W.COST_NONE)
+    op = replace(op, kl_eps=float("inf"), iters=95)
+    res = gpu_solve([pb], [op], FP64)[0]
+    pr = oracle.prior(pb)
+    assert rel_mu(res.mu, pr.mubar) < 1e-11
+    assert all(l["beta"] == 0.5 and l["trials"] == 1 for l in res.logs)
+
+
+def test_binding_kl_bound_and_options(pg):
+    """A KL bound tight enough to force the bisection; interior-only factors,
+    h^2/sigma^2 form, a temperature, and Lambda_0 = s I."""
+    pb, op = W.c1_point2d(N=30, iters=8)
+    op = replace(op, kl_eps=0.5)
+    res = gpu_solve([pb], [op], FP64)[0]
+    assert any(l["trials"] > 1 for l in res.logs)
+    compare_plan(pb, op, res, rtol_mu=1e-9, rtol_sigma=1e-9)
+    pb2 = replace(pb, factor_set=1, psi_form=1, temperature=3.0)
+    op2 = replace(op, init_kind=1, init_scale=50.0, kl_eps=0.1 * 31)
+    res2 = gpu_solve([pb2], [op2], FP64)[0]
+    compare_plan(pb2, op2, res2, rtol_mu=1e-9, rtol_sigma=1e-9)
+
+
+def test_batch_equals_alone_and_ragged(pg):
+    """Plans of different N in one batch give the same result as alone."""
+    probs = [W.c1_point2d(request=r, N=N, iters=6) for r, N in enumerate([7, 50, 33, 1, 64])]
+    pbs, ops = [p for p, _ in probs], [o for _, o in probs]
+    together = gpu_solve(pbs, ops, MIXED)
+    for i, (pb, op) in enumerate(probs):
+        alone = gpu_solve([pb], [op], MIXED)[0]
+        np.testing.assert_array_equal(together[i].mu, alone.mu)
+        np.testing.assert_array_equal(together[i].Sd, alone.Sd)
+
+
+def test_context_api_matches_batch(pg):
+    pb, op = W.c1_point2d(N=20, iters=5)
+    from paper_2411_03416_b300 import Context
+    ctx = Context(pb, op, MIXED)
+    infos = [ctx.step() for _ in range(2)]
+    ctx.plan(3)
+    mu, Sd, Ld, Lo = ctx.get()
+    ctx.close()
+    res = gpu_solve([pb], [op], MIXED)[0]
+    np.testing.assert_array_equal(mu, res.mu)
+    np.testing.assert_array_equal(Sd, res.Sd)
+    assert infos[0]["iter"] == 0 and infos[1]["iter"] == 1
+    assert infos[1]["beta"] == res.logs[1]["beta"]
