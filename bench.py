@@ -74,11 +74,11 @@ def fp64_flops_per_iter_state(n: int, dc: int) -> int:
     return 5 * n * n + dc ** 3 + 2 * dc * dc * dc + 2 * dc * dc + 4 * dc
 
 
-def algorithmic_fp64_flops(problems, trials_per_plan):
+def algorithmic_fp64_flops(problems, trials_per_plan, iters=ITERS):
     tot = 0
     for pb, trials in zip(problems, trials_per_plan):
         S = pb.N + 1
-        tot += S * (trials * fp64_flops_per_trial_state(pb.n) + ITERS * fp64_flops_per_iter_state(pb.n, 2))
+        tot += S * (trials * fp64_flops_per_trial_state(pb.n) + iters * fp64_flops_per_iter_state(pb.n, 2))
     return tot
 
 
@@ -87,6 +87,21 @@ def fp64_peak_tflops():
     SM per clock x 2 flops x 2032 MHz = 1.203 TFLOP/s (B300 data sheet 1.25).
     Measured with a DFMA-throughput loop on this machine: 0.935 TFLOP/s."""
     return 148 * 2 * 2 * 2.032e9 / 1e12
+
+
+def fp32_peak_tflops():
+    """FP32 peak derived from unit counts and clock: 148 SMs x 128 FFMA lanes per
+    SM per clock x 2 flops x 2032 MHz = 76.99 TFLOP/s.  Measured with an
+    FFMA-throughput loop on this machine: 68.2 TFLOP/s."""
+    return 148 * 128 * 2 * 2.032e9 / 1e12
+
+
+# FP32 flops per emulated FP64 flop in the double-float recursions, from the
+# implementation: a double-float FMA is 4 FFMA/FMUL + 11 FADD/FSUB (18 flops
+# for 2 FP64 flops), a multiply 10 flops, an add 11 flops; with the trial's
+# measured FP64 op mix (600 FMA : 129 add : 168 mul per state) that is
+# (600*18 + 129*11 + 168*10) / (600*2 + 129 + 168) = 9.29.
+DF_EXPANSION = 9.29
 
 
 # --------------------------------------------------------------------- clocks
@@ -231,6 +246,42 @@ def config_dict(batch, ws):
             "l2": "inputs larger than L2 (no flush needed)", "parallelism": f"replicas x{ws}"}
 
 
+PRECISIONS = {"fp64": 0, "mixed": 1, "mixed_df": 2}
+DTYPES = {0: "f64", 1: "f32 quadrature + f64 recursions",
+          2: "f32 quadrature + double-float (f32-pair, ~48-bit) recursions"}
+
+
+def kernel_only(args):
+    """One fused-iteration launch over a batch (an ncu target)."""
+    from dataclasses import replace
+
+    import torch
+
+    from paper_2411_03416_b300 import _lib as L
+    probs, opts = make_batch_problems(args.batch)
+    opts = [replace(o, iters=args.iters) for o in opts]
+    b = L.Batch(probs, opts, PRECISIONS[args.precision])
+    st = torch.cuda.Stream()
+    sh = st.cuda_stream
+    b.upload(sh)
+    b.reset(sh)
+    b.phase(L.PHASE_PRIOR, 0.0, sh)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    b.run(0, sh)
+    e1.record(st)
+    torch.cuda.synchronize()
+    b.download_results(sh)
+    torch.cuda.synchronize()
+    trials = [sum(l["trials"] for l in b.result(i, full=False).logs) for i in range(args.batch)]
+    ms = e0.elapsed_time(e1)
+    flops = algorithmic_fp64_flops(probs, trials, args.iters)
+    print(f"kernel-only: batch {args.batch}, {args.iters} iterations, {args.precision}: {ms:.1f} ms, "
+          f"{sum(trials)} trials, {flops / ms / 1e9:.4f} TFLOP/s-equivalent", flush=True)
+    b.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -240,9 +291,15 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--plain-steps", type=int, default=2)
+    ap.add_argument("--precision", default="mixed_df", choices=["mixed_df", "mixed", "fp64"])
+    ap.add_argument("--kernel-only", action="store_true",
+                    help="profiling target: prior phase, then one fused-iteration launch; no JSON line")
+    ap.add_argument("--iters", type=int, default=ITERS, help="proximal iterations (kernel-only mode)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.kernel_only:
+        return kernel_only(args)
 
     ws, rank, local = dist_init()
     cpu = None
@@ -266,12 +323,29 @@ def main():
         torch.cuda.synchronize()
         return b
 
+    def time_steps(precision, steps):
+        b = make(precision)
+        plan_step(b)
+        torch.cuda.synchronize()
+        times = []
+        for _ in range(steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            plan_step(b)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+        b.close()
+        ms = statistics.median(times)
+        return {"value": args.batch * ws / max_over_ranks(ws, ms / 1000.0), "unit": "plans/s", "ms_per_step": ms}
+
     def plan_step(b):
         b.reset(sh)
         b.run(0, sh)
 
-    # ---- served mixed precision, device-resident inputs
-    bm = make(L.PREC_MIXED)
+    # ---- served form, device-resident inputs
+    head = PRECISIONS[args.precision]
+    bm = make(head)
     for _ in range(args.warmup):
         plan_step(bm)
     torch.cuda.synchronize()
@@ -312,8 +386,18 @@ def main():
         trials.append(sum(l["trials"] for l in r.logs))
     flops = algorithmic_fp64_flops(probs, trials)
     k_ms = min(it_ms)
-    achieved = flops / (k_ms / 1000.0) / 1e12
-    peak = fp64_peak_tflops()
+    if head == 2:
+        flops32 = flops * DF_EXPANSION
+        achieved = flops32 / (k_ms / 1000.0) / 1e12
+        peak = fp32_peak_tflops()
+        roof_kind = ("FP32 pipe (double-float recursions): FP64-equivalent flops x 9.29 FP32 flops each; peak derived "
+                     "from unit counts and clock (measured FFMA loop: 68.2)")
+        kernel_name = "k_iterate<4, float, df64> (fused proximal iterations)"
+    else:
+        achieved = flops / (k_ms / 1000.0) / 1e12
+        peak = fp64_peak_tflops()
+        roof_kind = "FP64 derived from unit counts and clock (measured DFMA loop: 0.935)"
+        kernel_name = f"k_iterate<4, {'float' if head == 1 else 'double'}, double> (fused proximal iterations)"
 
     # ---- e2e through the C ABI with host buffers
     h2d, d2h_full, d2h = bm.io_bytes()
@@ -332,20 +416,14 @@ def main():
     e2e_value = args.batch * ws * args.steps / e2e_max
     bm.close()
 
-    # ---- plain FP64 path on the same batch
-    bp = make(L.PREC_PLAIN_FP64)
-    plan_step(bp)
-    torch.cuda.synchronize()
-    pe = []
-    for _ in range(args.plain_steps):
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        plan_step(bp)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        pe.append(e0.elapsed_time(e1))
-    bp.close()
-    plain_value = args.batch * ws / max_over_ranks(ws, statistics.median(pe) / 1000.0)
+    # ---- the other forms on the same batch
+    others = {}
+    if args.plain_steps > 0:
+        others["plain_fp64"] = time_steps(L.PREC_PLAIN_FP64, args.plain_steps)
+        if head != L.PREC_MIXED:
+            others["served_fp64_recursions"] = time_steps(L.PREC_MIXED, args.plain_steps)
+        if head != L.PREC_MIXED_DF:
+            others["served_double_float_recursions"] = time_steps(L.PREC_MIXED_DF, args.plain_steps)
 
     if rank != 0:
         return
@@ -356,11 +434,10 @@ def main():
         "config": config_dict(args.batch, ws),
         "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
                        "note": "batch latency: every plan of a step completes at the end of the step"},
-        "plain_fp64": {"value": plain_value, "unit": "plans/s", "ms_per_step": statistics.median(pe)},
+        **others,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                     "traffic": None, "kernel": "k_iterate<4, float> (fused proximal iterations)",
-                     "kernel_ms": k_ms, "peak_kind": "FP64 derived from unit counts and clock (measured DFMA loop: "
-                     "0.935)", "algorithmic_fp64_flops": flops},
+                     "traffic": None, "kernel": kernel_name, "kernel_ms": k_ms, "peak_kind": roof_kind,
+                     "algorithmic_fp64_equivalent_flops": flops},
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": "plans/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "ms_per_step": statistics.median(e2e_ms)},

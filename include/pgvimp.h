@@ -66,8 +66,12 @@ typedef enum { PGVIMP_RULE_GH = 0, PGVIMP_RULE_DEG3 = 1 } pgvimp_rule;
 
 /* Arithmetic of the path.  PLAIN_FP64: everything in FP64.  MIXED: the
  * quadrature, SDF and moment arithmetic in FP32 (FP32 accumulation); the
- * marginal recovery, the update and the KL / step-size search in FP64. */
-typedef enum { PGVIMP_PREC_PLAIN_FP64 = 0, PGVIMP_PREC_MIXED = 1 } pgvimp_precision;
+ * marginal recovery, the update and the KL / step-size search in FP64.
+ * MIXED_DF: as MIXED, but the recursions run in double-float arithmetic
+ * (pairs of FP32 values, ~48-bit significand) on the FP32 pipe, which on B300
+ * issues at 64x the FP64 rate; results are returned in FP64.  The single-row
+ * phases (pgvimp_batch_phase other than PRIOR) need PLAIN_FP64 or MIXED. */
+typedef enum { PGVIMP_PREC_PLAIN_FP64 = 0, PGVIMP_PREC_MIXED = 1, PGVIMP_PREC_MIXED_DF = 2 } pgvimp_precision;
 
 /* One planning problem.  All pointers are host pointers, row-major FP64
  * unless stated.  The state is x = [q; qdot], n = 2*nq. */

@@ -763,8 +763,15 @@ int ora_step(const ora_problem *pb, const ora_options *op, int k,
   } while (0)
   int feas = 0;
   if (op->replay_beta) {
+    /* replay: the step sizes are given (decided elsewhere); a step is taken
+     * whenever Lambda' is positive definite, whatever its KL */
     double bt = op->replay_beta[k];
-    if (bt > 0.0) TRY(bt, feas);
+    if (bt > 0.0) {
+      double eps_saved = eps;
+      eps = INFINITY;
+      TRY(bt, feas);
+      eps = eps_saved;
+    }
   } else {
     TRY(op->beta_max, feas);
     if (!feas) {

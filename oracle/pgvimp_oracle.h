@@ -80,7 +80,7 @@ typedef struct {
   int slr_iters;
   int init_kind;            /* 0: Lambda0 = K^-1; 1: Lambda0 = init_scale * I */
   double init_scale;
-  const double *replay_beta;/* if non-NULL: accept these beta_k without search */
+  const double *replay_beta;/* if non-NULL: take these beta_k (no search, no KL test) */
 } ora_options;
 
 typedef struct {

@@ -17,7 +17,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.environ.get("PGVIMP_LIB") or os.path.join(_HERE, "_build", "libpgvimp.so")
 
 OK, EINVAL, ENOMEM, ENOTPD, ECUDA, ETIMEOUT, EBUSY, ENOTFINITE, ENOTREADY = range(9)
-PREC_PLAIN_FP64, PREC_MIXED = 0, 1
+PREC_PLAIN_FP64, PREC_MIXED, PREC_MIXED_DF = 0, 1, 2
 PHASE_PRIOR, PHASE_MARGINALS, PHASE_QUAD, PHASE_TRIAL, PHASE_SLR = range(5)
 (BUF_MU, BUF_LD, BUF_LO, BUF_SD, BUF_SO, BUF_KD, BUF_KO, BUF_B, BUF_G1, BUF_G2, BUF_TMU, BUF_TSD, BUF_TSO,
  BUF_ALTV, BUF_ALTVA, BUF_SCAL) = range(16)

@@ -17,7 +17,8 @@ OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libpgvimp.so")
 ROOT = os.path.dirname(HERE)
 
-SOURCES = ["pgvimp_api.cu"] + [f"k{n}_{part}.cu" for n in (14, 6, 4) for part in ("iter_f32", "iter_f64", "aux", "rows")]
+SOURCES = ["pgvimp_api.cu"] + [f"k{n}_{part}.cu" for n in (6, 4, 14)
+                               for part in ("iter_df", "iter_f32", "iter_f64", "aux", "aux_df", "rows")]
 HEADERS = ["pgvimp_device.cuh", "pgvimp_kernels.cuh", "pgvimp_plan.h", "pgvimp_launch.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "-I", os.path.join(ROOT, "include")]

@@ -1,6 +1,6 @@
-// Fused proximal iterations, state dimension 14, FP32 quadrature.
+// State dimension 14: fused iterations, FP32 quadrature, FP64 recursions.
 #include "pgvimp_kernels.cuh"
 
 namespace pgv {
-template cudaError_t launch_iter<14, float>(const Launch& L, int iters);
+template cudaError_t launch_iter<14, float, double>(const Launch& L, int iters);
 }  // namespace pgv

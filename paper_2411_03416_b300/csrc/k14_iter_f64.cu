@@ -1,6 +1,6 @@
-// Fused proximal iterations, state dimension 14, FP64 quadrature.
+// State dimension 14: fused iterations, FP64 quadrature and recursions.
 #include "pgvimp_kernels.cuh"
 
 namespace pgv {
-template cudaError_t launch_iter<14, double>(const Launch& L, int iters);
+template cudaError_t launch_iter<14, double, double>(const Launch& L, int iters);
 }  // namespace pgv

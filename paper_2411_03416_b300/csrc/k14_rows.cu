@@ -1,4 +1,4 @@
-// Single-row kernels (marginals, quadrature, one trial), state dimension 14.
+// State dimension 14: single-row kernels (marginals, quadrature, one trial).
 #include "pgvimp_kernels.cuh"
 
 namespace pgv {

@@ -1,6 +1,6 @@
-// Fused proximal iterations, state dimension 4, FP32 quadrature.
+// State dimension 4: fused iterations, FP32 quadrature, FP64 recursions.
 #include "pgvimp_kernels.cuh"
 
 namespace pgv {
-template cudaError_t launch_iter<4, float>(const Launch& L, int iters);
+template cudaError_t launch_iter<4, float, double>(const Launch& L, int iters);
 }  // namespace pgv

@@ -1,6 +1,6 @@
-// Fused proximal iterations, state dimension 4, FP64 quadrature.
+// State dimension 4: fused iterations, FP64 quadrature and recursions.
 #include "pgvimp_kernels.cuh"
 
 namespace pgv {
-template cudaError_t launch_iter<4, double>(const Launch& L, int iters);
+template cudaError_t launch_iter<4, double, double>(const Launch& L, int iters);
 }  // namespace pgv

@@ -1,6 +1,6 @@
-// Prior build, initial iterate, SLR and bookkeeping kernels, state dimension 6.
+// State dimension 6: prior build, initial iterate, SLR and bookkeeping kernels (FP64 recursions).
 #include "pgvimp_kernels.cuh"
 
 namespace pgv {
-template cudaError_t launch_aux<6>(const Launch& L, int phase, int arg_i, int mixed);
+template cudaError_t launch_aux<6, double>(const Launch& L, int phase, int arg_i, int qt32);
 }  // namespace pgv

@@ -1,6 +1,6 @@
-// Fused proximal iterations, state dimension 6, FP64 quadrature.
+// State dimension 6: fused iterations, FP64 quadrature and recursions.
 #include "pgvimp_kernels.cuh"
 
 namespace pgv {
-template cudaError_t launch_iter<6, double>(const Launch& L, int iters);
+template cudaError_t launch_iter<6, double, double>(const Launch& L, int iters);
 }  // namespace pgv

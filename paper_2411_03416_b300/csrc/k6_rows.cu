@@ -1,4 +1,4 @@
-// Single-row kernels (marginals, quadrature, one trial), state dimension 6.
+// State dimension 6: single-row kernels (marginals, quadrature, one trial).
 #include "pgvimp_kernels.cuh"
 
 namespace pgv {

@@ -16,16 +16,21 @@
 #include "pgvimp_launch.h"
 
 namespace pgv {
-// Dispatch of a phase to the kernels of state dimension n.
-static cudaError_t launch_phase(int n, const Launch& L, int phase, int arg_i, double arg_d, int mixed) {
+// Dispatch of a phase to the kernels of state dimension n and precision.
+static cudaError_t launch_phase(int n, const Launch& L, int phase, int arg_i, double arg_d, int precision) {
   constexpr int ITER = 102;
   const bool rows = (phase == PGVIMP_PHASE_MARGINALS || phase == PGVIMP_PHASE_QUAD || phase == PGVIMP_PHASE_TRIAL);
+  const bool df = (precision == PGVIMP_PREC_MIXED_DF);
+  const int qt32 = (precision != PGVIMP_PREC_PLAIN_FP64);
   switch (n) {
-#define PGV_CASE(N_)                                                                       \
-  case N_:                                                                                 \
-    if (phase == ITER) return mixed ? launch_iter<N_, float>(L, arg_i) : launch_iter<N_, double>(L, arg_i); \
-    if (rows) return launch_rows<N_>(L, phase, arg_d, mixed);                              \
-    return launch_aux<N_>(L, phase, arg_i, mixed);
+#define PGV_CASE(N_)                                                                                      \
+  case N_:                                                                                                \
+    if (phase == ITER) {                                                                                  \
+      if (df) return launch_iter<N_, float, df64>(L, arg_i);                                              \
+      return qt32 ? launch_iter<N_, float, double>(L, arg_i) : launch_iter<N_, double, double>(L, arg_i); \
+    }                                                                                                     \
+    if (rows) return launch_rows<N_>(L, phase, arg_d, qt32);                                              \
+    return df ? launch_aux<N_, df64>(L, phase, arg_i, qt32) : launch_aux<N_, double>(L, phase, arg_i, qt32);
     PGV_CASE(4)
     PGV_CASE(6)
     PGV_CASE(14)
@@ -47,7 +52,8 @@ pgvimp_status fail(std::string* where, pgvimp_status st, const std::string& msg)
   return st;
 }
 
-constexpr int PH_PRIOR = 100, PH_INIT = 101, PH_ITER = 102, PH_SLR = 103, PH_RELIN = 104, PH_SLR_FIN = 105;
+constexpr int PH_PRIOR = 100, PH_INIT = 101, PH_ITER = 102, PH_SLR = 103, PH_RELIN = 104, PH_SLR_FIN = 105,
+              PH_FINALIZE = 106, PH_WORKING = 107;
 
 // ------------------------------------------------------------ GH rule tables
 // Golub-Welsch: the nodes of the p-point rule for the N(0,1) weight are the
@@ -457,7 +463,7 @@ pgvimp_status cuda_fail(std::string* err, cudaError_t e, const char* what) {
 
 pgvimp_status launch(BatchImpl& B, int phase, int arg_i, double arg_d, cudaStream_t s) {
   Launch L{reinterpret_cast<const PlanDesc*>(B.d_in() + B.off_desc), B.count, s};
-  cudaError_t e = launch_phase(B.n, L, phase, arg_i, arg_d, B.precision == PGVIMP_PREC_MIXED);
+  cudaError_t e = launch_phase(B.n, L, phase, arg_i, arg_d, B.precision);
   if (e != cudaSuccess) return cuda_fail(&B.err, e, "kernel launch");
   return PGVIMP_OK;
 }
@@ -500,7 +506,8 @@ const char* pgvimp_last_error(const void* ctx) {
 static pgvimp_status prepare(int count, const pgvimp_problem* problems, const pgvimp_options* options, int precision,
                              BatchImpl& B) {
   if (count < 1 || !problems || !options) return fail(&B.err, PGVIMP_EINVAL, "count must be >= 1 with problems and options");
-  if (precision != PGVIMP_PREC_PLAIN_FP64 && precision != PGVIMP_PREC_MIXED) return fail(&B.err, PGVIMP_EINVAL, "unknown precision");
+  if (precision != PGVIMP_PREC_PLAIN_FP64 && precision != PGVIMP_PREC_MIXED && precision != PGVIMP_PREC_MIXED_DF)
+    return fail(&B.err, PGVIMP_EINVAL, "unknown precision");
   for (int i = 0; i < count; ++i) {
     pgvimp_status st = validate(problems[i], options[i], i, &B.err);
     if (st != PGVIMP_OK) return st;
@@ -604,6 +611,7 @@ pgvimp_status pgvimp_batch_run(pgvimp_batch* b, int iters, void* stream) {
   if (!b) return fail(nullptr, PGVIMP_EINVAL, "batch is NULL");
   cudaStream_t s = (cudaStream_t)stream;
   pgvimp_status st;
+  if (b->started && b->precision == PGVIMP_PREC_MIXED_DF && (st = launch(*b, PH_WORKING, 0, 0.0, s))) return st;
   if (b->dyn == PGVIMP_DYN_LINEAR) {
     if (!b->started) {
       if ((st = launch(*b, PH_PRIOR, 0, 0.0, s))) return st;
@@ -650,6 +658,8 @@ pgvimp_status pgvimp_batch_phase(pgvimp_batch* b, int phase, double arg, void* s
   if (!b) return fail(nullptr, PGVIMP_EINVAL, "batch is NULL");
   cudaStream_t s = (cudaStream_t)stream;
   pgvimp_status st;
+  if (b->precision == PGVIMP_PREC_MIXED_DF && phase != PGVIMP_PHASE_PRIOR)
+    return fail(&b->err, PGVIMP_EINVAL, "single-row phases run with FP64 or mixed recursions only");
   switch (phase) {
     case PGVIMP_PHASE_PRIOR:
       if (b->dyn != PGVIMP_DYN_LINEAR) {
@@ -725,13 +735,21 @@ pgvimp_status pgvimp_batch_destroy(pgvimp_batch* b) {
   return PGVIMP_OK;
 }
 
-static pgvimp_status resolve(const pgvimp_batch* b, int index, int buffer, double** dptr, size_t* cnt) {
+// Device location and element count of a plan buffer; `pairs` tells whether
+// it currently holds double-float pairs (double-float storage) or FP64.
+static pgvimp_status resolve(const pgvimp_batch* b, int index, int buffer, double** dptr, size_t* cnt,
+                             bool* pairs) {
   if (!b || index < 0 || index >= b->count) return fail(nullptr, PGVIMP_EINVAL, "bad batch or index");
   const PlanDesc& d = b->desc[index];
   const size_t n = d.n, N = d.N, nn = n * n;
   double scal[kScal];
   cudaError_t e = cudaMemcpy(scal, d.scal, sizeof(scal), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return fail(nullptr, PGVIMP_ECUDA, std::string("read scalars: ") + cudaGetErrorString(e));
+  const bool result_fp64 = scal[S_FMT] == 1.0 &&
+                           (buffer == PGVIMP_BUF_MU || buffer == PGVIMP_BUF_SD || buffer == PGVIMP_BUF_SO ||
+                            buffer == PGVIMP_BUF_LD || buffer == PGVIMP_BUF_LO);
+  *pairs = b->precision == PGVIMP_PREC_MIXED_DF && buffer != PGVIMP_BUF_SCAL && buffer != PGVIMP_BUF_ALTV &&
+           buffer != PGVIMP_BUF_ALTVA && !result_fp64;
   const int cur = (int)scal[S_CUR] % 3, tr = (cur + 2) % 3;
   switch (buffer) {
     case PGVIMP_BUF_MU: *dptr = d.mu[cur]; *cnt = (N + 1) * n; break;
@@ -762,21 +780,41 @@ static pgvimp_status resolve(const pgvimp_batch* b, int index, int buffer, doubl
 pgvimp_status pgvimp_batch_read(const pgvimp_batch* b, int index, int buffer, double* host, size_t count) {
   double* d;
   size_t c;
-  pgvimp_status st = resolve(b, index, buffer, &d, &c);
+  bool pairs;
+  pgvimp_status st = resolve(b, index, buffer, &d, &c, &pairs);
   if (st) return st;
   if (!host || count != c) return fail(nullptr, PGVIMP_EINVAL, "count does not match the buffer size");
   cudaError_t e = cudaMemcpy(host, d, 8 * c, cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return fail(nullptr, PGVIMP_ECUDA, std::string("read: ") + cudaGetErrorString(e));
+  if (pairs)
+    for (size_t k = 0; k < c; ++k) {
+      float hl[2];
+      std::memcpy(hl, host + k, sizeof(hl));
+      host[k] = (double)hl[0] + (double)hl[1];
+    }
   return PGVIMP_OK;
 }
 
 pgvimp_status pgvimp_batch_write(pgvimp_batch* b, int index, int buffer, const double* host, size_t count) {
   double* d;
   size_t c;
-  pgvimp_status st = resolve(b, index, buffer, &d, &c);
+  bool pairs;
+  pgvimp_status st = resolve(b, index, buffer, &d, &c, &pairs);
   if (st) return st;
   if (!host || count != c) return fail(nullptr, PGVIMP_EINVAL, "count does not match the buffer size");
-  cudaError_t e = cudaMemcpy(d, host, 8 * c, cudaMemcpyHostToDevice);
+  std::vector<double> tmp;
+  const double* src = host;
+  if (pairs) {
+    tmp.resize(c);
+    for (size_t k = 0; k < c; ++k) {
+      float hl[2];
+      hl[0] = (float)host[k];
+      hl[1] = (float)(host[k] - (double)hl[0]);
+      std::memcpy(&tmp[k], hl, sizeof(hl));
+    }
+    src = tmp.data();
+  }
+  cudaError_t e = cudaMemcpy(d, src, 8 * c, cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return fail(nullptr, PGVIMP_ECUDA, std::string("write: ") + cudaGetErrorString(e));
   return PGVIMP_OK;
 }
@@ -859,6 +897,7 @@ pgvimp_status pgvimp_destroy(pgvimp_ctx* c) {
 }  // extern "C"
 
 static pgvimp_status finalize(pgvimp_batch* b, cudaStream_t s) {
-  // The iterate may sit in buffer set 1 or 2; results are read from set 0.
-  return launch(*b, 106, 0, 0.0, s);
+  // The iterate may sit in buffer set 1 or 2; results are read from set 0
+  // (and, with double-float storage, converted to FP64 in place).
+  return launch(*b, PH_FINALIZE, 0, 0.0, s);
 }

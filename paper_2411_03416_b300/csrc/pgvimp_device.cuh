@@ -44,135 +44,321 @@ __host__ __device__ __forceinline__ double pgv_rsqrt(double x) {
 #endif
 }
 
-// ------------------------------------------------------------ small blocks
-// Row-major n x n blocks held in thread-local arrays.
+// ------------------------------------------------------------ double-float
+// FP64-class arithmetic on the FP32 pipe: a value is the unevaluated sum
+// hi + lo of two floats (|lo| <= ulp(hi)/2, ~48-bit significand), combined
+// with the error-free transformations of Knuth (two-sum), Dekker (fast
+// two-sum) and the FMA two-product.  The intrinsics below are never
+// contracted into FMAs, which the transformations rely on.  B300 issues FP32
+// at 64x its FP64 rate and with 4-cycle instead of 64-cycle latency.
+#ifdef __CUDA_ARCH__
+#define PGV_FADD(a, b) __fadd_rn(a, b)
+#define PGV_FSUB(a, b) __fsub_rn(a, b)
+#define PGV_FMUL(a, b) __fmul_rn(a, b)
+#define PGV_FFMA(a, b, c) __fmaf_rn(a, b, c)
+#else
+#define PGV_FADD(a, b) ((a) + (b))
+#define PGV_FSUB(a, b) ((a) - (b))
+#define PGV_FMUL(a, b) ((a) * (b))
+#define PGV_FFMA(a, b, c) fmaf(a, b, c)
+#endif
+#define PGV_HD __host__ __device__ __forceinline__
 
-template <int n>
-PGV_DEV void ld_blk(const double* p, double* X) {
-  const double2* q = reinterpret_cast<const double2*>(p);
-#pragma unroll (n <= 8 ? 32 : 1)
-  for (int e = 0; e < n * n / 2; ++e) {
-    double2 v = q[e];
-    X[2 * e] = v.x;
-    X[2 * e + 1] = v.y;
-  }
-}
-template <int n>
-PGV_DEV void st_blk(double* p, const double* X) {
-  double2* q = reinterpret_cast<double2*>(p);
-#pragma unroll (n <= 8 ? 32 : 1)
-  for (int e = 0; e < n * n / 2; ++e) q[e] = make_double2(X[2 * e], X[2 * e + 1]);
-}
-template <int n>
-PGV_DEV void st_blk_scaled(double* p, const double* X, double s) {
-  double2* q = reinterpret_cast<double2*>(p);
-#pragma unroll (n <= 8 ? 32 : 1)
-  for (int e = 0; e < n * n / 2; ++e) q[e] = make_double2(s * X[2 * e], s * X[2 * e + 1]);
-}
-template <int n>
-PGV_DEV void ld_vec(const double* p, double* x) {
-#pragma unroll (n <= 8 ? 32 : 1)
-  for (int a = 0; a < n; ++a) x[a] = p[a];
-}
-template <int n>
-PGV_DEV void st_vec(double* p, const double* x) {
-#pragma unroll (n <= 8 ? 32 : 1)
-  for (int a = 0; a < n; ++a) p[a] = x[a];
-}
+struct __align__(8) df64 {
+  float hi, lo;
+};
 
-// Y = X * Cinv with Cinv symmetric (full storage).
-template <int n>
-PGV_DEV void mul_nn(const double* X, const double* Y, double* Z) {
-#pragma unroll (n <= 8 ? 32 : 1)
-  for (int a = 0; a < n; ++a)
-#pragma unroll (n <= 8 ? 32 : 1)
-    for (int c = 0; c < n; ++c) {
-      double s = 0.0;
-#pragma unroll (n <= 8 ? 32 : 1)
-      for (int t = 0; t < n; ++t) s = fma(X[a * n + t], Y[t * n + c], s);
-      Z[a * n + c] = s;
-    }
+PGV_HD df64 df_make(float h, float l) {
+  df64 r;
+  r.hi = h;
+  r.lo = l;
+  return r;
 }
-// Z = X * Y^T, symmetric result assumed (lower computed, mirrored).
-template <int n>
-PGV_DEV void mul_nt_sym(const double* X, const double* Y, double* Z) {
-#pragma unroll (n <= 8 ? 32 : 1)
-  for (int a = 0; a < n; ++a)
-#pragma unroll (n <= 8 ? 32 : 1)
-    for (int c = 0; c <= a; ++c) {
-      double s = 0.0;
-#pragma unroll (n <= 8 ? 32 : 1)
-      for (int t = 0; t < n; ++t) s = fma(X[a * n + t], Y[c * n + t], s);
-      Z[a * n + c] = s;
-      Z[c * n + a] = s;
-    }
+PGV_HD df64 df_fast_two_sum(float a, float b) {  // |a| >= |b|
+  float s = PGV_FADD(a, b);
+  return df_make(s, PGV_FSUB(b, PGV_FSUB(s, a)));
 }
-// Z = C + X^T Y, symmetric result assumed.
-template <int n>
-PGV_DEV void add_tn_sym(const double* C, const double* X, const double* Y, double* Z) {
-#pragma unroll (n <= 8 ? 32 : 1)
-  for (int a = 0; a < n; ++a)
-#pragma unroll (n <= 8 ? 32 : 1)
-    for (int c = 0; c <= a; ++c) {
-      double s = C[a * n + c];
-#pragma unroll (n <= 8 ? 32 : 1)
-      for (int t = 0; t < n; ++t) s = fma(X[t * n + a], Y[t * n + c], s);
-      Z[a * n + c] = s;
-      Z[c * n + a] = s;
-    }
+PGV_HD df64 operator+(df64 x, df64 y) {
+  float s = PGV_FADD(x.hi, y.hi);
+  float bb = PGV_FSUB(s, x.hi);
+  float e = PGV_FADD(PGV_FSUB(x.hi, PGV_FSUB(s, bb)), PGV_FSUB(y.hi, bb));
+  e = PGV_FADD(e, PGV_FADD(x.lo, y.lo));
+  return df_fast_two_sum(s, e);
+}
+PGV_HD df64 operator-(df64 x) { return df_make(-x.hi, -x.lo); }
+PGV_HD df64 operator-(df64 x, df64 y) { return x + (-y); }
+PGV_HD df64 operator*(df64 x, df64 y) {
+  float p = PGV_FMUL(x.hi, y.hi);
+  float e = PGV_FFMA(x.hi, y.hi, -p);
+  e = PGV_FFMA(x.hi, y.lo, e);
+  e = PGV_FFMA(x.lo, y.hi, e);
+  return df_fast_two_sum(p, e);
+}
+// x * y + z with one normalisation.
+PGV_HD df64 df_fma(df64 x, df64 y, df64 z) {
+  float p = PGV_FMUL(x.hi, y.hi);
+  float e = PGV_FFMA(x.hi, y.hi, -p);
+  e = PGV_FFMA(x.hi, y.lo, e);
+  e = PGV_FFMA(x.lo, y.hi, e);
+  float s = PGV_FADD(p, z.hi);
+  float bb = PGV_FSUB(s, p);
+  float f = PGV_FADD(PGV_FSUB(p, PGV_FSUB(s, bb)), PGV_FSUB(z.hi, bb));
+  f = PGV_FADD(f, PGV_FADD(e, z.lo));
+  return df_fast_two_sum(s, f);
 }
 
-// Accumulates pivot products as mantissa * 2^exponent so that log det needs a
-// single log at the end of a sweep.
-struct LogDetAcc {
+// Arithmetic used by the recursions, for R = double (native FP64) and
+// R = df64 (double-float).
+PGV_HD double r_fma(double a, double b, double c) { return fma(a, b, c); }
+PGV_HD df64 r_fma(df64 a, df64 b, df64 c) { return df_fma(a, b, c); }
+template <typename R> PGV_HD R r_from(double v);
+template <> PGV_HD double r_from<double>(double v) { return v; }
+template <> PGV_HD df64 r_from<df64>(double v) {
+  float h = (float)v;
+  return df_make(h, (float)(v - (double)h));
+}
+template <typename R> PGV_HD R r_fromf(float v);
+template <> PGV_HD double r_fromf<double>(float v) { return (double)v; }
+template <> PGV_HD df64 r_fromf<df64>(float v) { return df_make(v, 0.0f); }
+PGV_HD double r_to(double v) { return v; }
+PGV_HD double r_to(df64 v) { return (double)v.hi + (double)v.lo; }
+PGV_HD float r_tof(double v) { return (float)v; }
+PGV_HD float r_tof(df64 v) { return v.hi + v.lo; }
+PGV_HD bool r_pos(double v) { return v > 0.0; }
+PGV_HD bool r_pos(df64 v) { return v.hi > 0.0f; }
+PGV_HD double r_rsqrt(double v) {
+#ifdef __CUDA_ARCH__
+  return rsqrt(v);
+#else
+  return 1.0 / sqrt(v);
+#endif
+}
+// 1/sqrt(v): FP32 estimate refined by one Newton step in double-float.
+PGV_HD df64 r_rsqrt(df64 v) {
+#ifdef __CUDA_ARCH__
+  float r0 = rsqrtf(v.hi);
+#else
+  float r0 = 1.0f / sqrtf(v.hi);
+#endif
+  df64 r = df_make(r0, 0.0f);
+  df64 u = (v * r) * r;                        // ~1
+  df64 d = df_make(1.0f, 0.0f) - u;            // small, accurate
+  return df_fma(df_make(0.5f * r0, 0.0f), d, r);
+}
+
+// log det accumulator: pivot products kept as mantissa * 2^expo.
+template <typename R>
+struct LogDetAcc;
+template <>
+struct LogDetAcc<double> {
   double mant;
   int expo;
-  PGV_DEV void init() { mant = 1.0; expo = 0; }
-  PGV_DEV void mul(double v) {
+  PGV_HD void init() { mant = 1.0; expo = 0; }
+  PGV_HD void mul(double v) {
     int e;
     mant = frexp(mant * v, &e);
     expo += e;
   }
-  PGV_DEV double log_value() const { return log(mant) + expo * 0.69314718055994530942; }
+  PGV_HD double log_value() const { return log(mant) + expo * 0.69314718055994530942; }
+};
+template <>
+struct LogDetAcc<df64> {
+  df64 mant;
+  int expo;
+  PGV_HD void init() { mant = df_make(1.0f, 0.0f); expo = 0; }
+  PGV_HD void mul(df64 v) {
+    mant = mant * v;
+    int e;
+    frexpf(mant.hi, &e);
+    mant.hi = ldexpf(mant.hi, -e);
+    mant.lo = ldexpf(mant.lo, -e);
+    expo += e;
+  }
+  PGV_HD double log_value() const { return log(r_to(mant)) + expo * 0.69314718055994530942; }
 };
 
-// Cholesky C = L L^T of a symmetric block, then Cinv = L^-T L^-1.
-// Returns false (and leaves Cinv undefined) unless every pivot is > 0.
+// ------------------------------------------------------------ small blocks
+// Row-major n x n blocks in global memory; symmetric blocks held in thread
+// registers in packed lower form, element (a, c) with c <= a at a(a+1)/2 + c.
+#define PGV_UNR _Pragma("unroll")
+
 template <int n>
-PGV_DEV bool chol_inverse(const double* C, double* Cinv, LogDetAcc& ld) {
-  double L[n * n];
-  double r[n];
-  bool ok = true;
+struct Blk {
+  static constexpr int nn = n * n;
+  static constexpr int np = n * (n + 1) / 2;
+};
+PGV_HD constexpr int pk(int a, int c) { return a >= c ? a * (a + 1) / 2 + c : c * (c + 1) / 2 + a; }
+
+// 16-byte vector access to pairs of 8-byte values (double or df64).
+template <typename R>
+struct __align__(16) Pair2 {
+  R a, b;
+};
+
+template <int n, typename R>
+PGV_DEV void ld_blk(const R* p, R* X) {
+  const Pair2<R>* q = reinterpret_cast<const Pair2<R>*>(p);
+#pragma unroll (n <= 8 ? 32 : 1)
+  for (int e = 0; e < n * n / 2; ++e) {
+    Pair2<R> v = q[e];
+    X[2 * e] = v.a;
+    X[2 * e + 1] = v.b;
+  }
+}
+template <int n, typename R>
+PGV_DEV void st_blk(R* p, const R* X) {
+  Pair2<R>* q = reinterpret_cast<Pair2<R>*>(p);
+#pragma unroll (n <= 8 ? 32 : 1)
+  for (int e = 0; e < n * n / 2; ++e) {
+    Pair2<R> v;
+    v.a = X[2 * e];
+    v.b = X[2 * e + 1];
+    q[e] = v;
+  }
+}
+// symmetric packed <-> full block in memory
+template <int n, typename R>
+PGV_DEV void ld_sym(const R* p, R* S) {
+  R X[n * n];
+  ld_blk<n, R>(p, X);
+#pragma unroll (n <= 8 ? 32 : 1)
+  for (int a = 0; a < n; ++a)
+#pragma unroll (n <= 8 ? 32 : 1)
+    for (int c = 0; c <= a; ++c) S[pk(a, c)] = X[a * n + c];
+}
+template <int n, typename R>
+PGV_DEV void st_sym(R* p, const R* S) {
+  R X[n * n];
+#pragma unroll (n <= 8 ? 32 : 1)
+  for (int a = 0; a < n; ++a)
+#pragma unroll (n <= 8 ? 32 : 1)
+    for (int c = 0; c < n; ++c) X[a * n + c] = S[pk(a, c)];
+  st_blk<n, R>(p, X);
+}
+// packed storage of length np rounded up to a whole 16-byte pair
+template <int n, typename R>
+PGV_DEV void ld_packed(const R* p, R* S) {
+  const Pair2<R>* q = reinterpret_cast<const Pair2<R>*>(p);
+  constexpr int np = n * (n + 1) / 2;
+#pragma unroll (n <= 8 ? 32 : 1)
+  for (int e = 0; e < (np + 1) / 2; ++e) {
+    Pair2<R> v = q[e];
+    S[2 * e] = v.a;
+    if (2 * e + 1 < np) S[2 * e + 1] = v.b;
+  }
+}
+template <int n, typename R>
+PGV_DEV void st_packed(R* p, const R* S) {
+  Pair2<R>* q = reinterpret_cast<Pair2<R>*>(p);
+  constexpr int np = n * (n + 1) / 2;
+#pragma unroll (n <= 8 ? 32 : 1)
+  for (int e = 0; e < (np + 1) / 2; ++e) {
+    Pair2<R> v;
+    v.a = S[2 * e];
+    v.b = (2 * e + 1 < np) ? S[2 * e + 1] : S[2 * e];
+    q[e] = v;
+  }
+}
+template <int n, typename R>
+PGV_DEV void ld_vec(const R* p, R* x) {
+#pragma unroll (n <= 8 ? 32 : 1)
+  for (int a = 0; a < n; ++a) x[a] = p[a];
+}
+template <int n, typename R>
+PGV_DEV void st_vec(R* p, const R* x) {
+#pragma unroll (n <= 8 ? 32 : 1)
+  for (int a = 0; a < n; ++a) p[a] = x[a];
+}
+
+// Z = X * S with S symmetric packed (full n x n result).
+template <int n, typename R>
+PGV_DEV void mul_full_sym(const R* X, const R* S, R* Z) {
+#pragma unroll (n <= 8 ? 32 : 1)
+  for (int a = 0; a < n; ++a)
+#pragma unroll (n <= 8 ? 32 : 1)
+    for (int c = 0; c < n; ++c) {
+      R s = X[a * n] * S[pk(0, c)];
+#pragma unroll (n <= 8 ? 32 : 1)
+      for (int t = 1; t < n; ++t) s = r_fma(X[a * n + t], S[pk(t, c)], s);
+      Z[a * n + c] = s;
+    }
+}
+// Z = S * X with S symmetric packed.
+template <int n, typename R>
+PGV_DEV void mul_sym_full(const R* S, const R* X, R* Z) {
+#pragma unroll (n <= 8 ? 32 : 1)
+  for (int a = 0; a < n; ++a)
+#pragma unroll (n <= 8 ? 32 : 1)
+    for (int c = 0; c < n; ++c) {
+      R s = S[pk(a, 0)] * X[c];
+#pragma unroll (n <= 8 ? 32 : 1)
+      for (int t = 1; t < n; ++t) s = r_fma(S[pk(a, t)], X[t * n + c], s);
+      Z[a * n + c] = s;
+    }
+}
+// packed Z = X * Y^T for a product known to be symmetric.
+template <int n, typename R>
+PGV_DEV void mul_nt_packed(const R* X, const R* Y, R* Z) {
+#pragma unroll (n <= 8 ? 32 : 1)
+  for (int a = 0; a < n; ++a)
+#pragma unroll (n <= 8 ? 32 : 1)
+    for (int c = 0; c <= a; ++c) {
+      R s = X[a * n] * Y[c * n];
+#pragma unroll (n <= 8 ? 32 : 1)
+      for (int t = 1; t < n; ++t) s = r_fma(X[a * n + t], Y[c * n + t], s);
+      Z[pk(a, c)] = s;
+    }
+}
+// packed Z = C + X^T Y (symmetric result).
+template <int n, typename R>
+PGV_DEV void add_tn_packed(const R* C, const R* X, const R* Y, R* Z) {
+#pragma unroll (n <= 8 ? 32 : 1)
+  for (int a = 0; a < n; ++a)
+#pragma unroll (n <= 8 ? 32 : 1)
+    for (int c = 0; c <= a; ++c) {
+      R s = C[pk(a, c)];
+#pragma unroll (n <= 8 ? 32 : 1)
+      for (int t = 0; t < n; ++t) s = r_fma(X[t * n + a], Y[t * n + c], s);
+      Z[pk(a, c)] = s;
+    }
+}
+
+// Cholesky C = L L^T of a packed symmetric block, then Cinv = L^-T L^-1
+// (packed).  `ok` is cleared unless every pivot is > 0; pivots feed `ld`.
+template <int n, typename R>
+PGV_DEV void chol_inverse(const R* C, R* Cinv, LogDetAcc<R>& ld, bool& ok) {
+  constexpr int np = n * (n + 1) / 2;
+  R L[np], r[n];
 #pragma unroll (n <= 8 ? 32 : 1)
   for (int j = 0; j < n; ++j) {
-    double s = C[j * n + j];
+    R s = C[pk(j, j)];
 #pragma unroll (n <= 8 ? 32 : 1)
-    for (int k = 0; k < j; ++k) s = fma(-L[j * n + k], L[j * n + k], s);
-    ok = ok && (s > 0.0);
-    s = ok ? s : 1.0;
-    double rs = pgv_rsqrt(s);
+    for (int k = 0; k < j; ++k) s = r_fma(-L[pk(j, k)], L[pk(j, k)], s);
+    ok = ok && r_pos(s);
+    s = r_pos(s) ? s : r_fromf<R>(1.0f);
+    R rs = r_rsqrt(s);
     r[j] = rs;
-    L[j * n + j] = s * rs;
     ld.mul(s);
 #pragma unroll (n <= 8 ? 32 : 1)
     for (int i = j + 1; i < n; ++i) {
-      double t = C[i * n + j];
+      R t = C[pk(i, j)];
 #pragma unroll (n <= 8 ? 32 : 1)
-      for (int k = 0; k < j; ++k) t = fma(-L[i * n + k], L[j * n + k], t);
-      L[i * n + j] = t * rs;
+      for (int k = 0; k < j; ++k) t = r_fma(-L[pk(i, k)], L[pk(j, k)], t);
+      L[pk(i, j)] = t * rs;
     }
+    L[pk(j, j)] = s * rs;
   }
-  // X = L^-1 (lower), stored over L's strictly-upper-free layout in Xi
-  double X[n * n];
+  // X = L^-1 (lower, packed)
+  R X[np];
 #pragma unroll (n <= 8 ? 32 : 1)
   for (int j = 0; j < n; ++j) {
-    X[j * n + j] = r[j];
+    X[pk(j, j)] = r[j];
 #pragma unroll (n <= 8 ? 32 : 1)
     for (int i = j + 1; i < n; ++i) {
-      double s = 0.0;
+      R s = L[pk(i, j)] * X[pk(j, j)];
 #pragma unroll (n <= 8 ? 32 : 1)
-      for (int k = j; k < i; ++k) s = fma(L[i * n + k], X[k * n + j], s);
-      X[i * n + j] = -s * r[i];
+      for (int k = j + 1; k < i; ++k) s = r_fma(L[pk(i, k)], X[pk(k, j)], s);
+      X[pk(i, j)] = -(s * r[i]);
     }
   }
   // Cinv = X^T X
@@ -180,45 +366,42 @@ PGV_DEV bool chol_inverse(const double* C, double* Cinv, LogDetAcc& ld) {
   for (int a = 0; a < n; ++a)
 #pragma unroll (n <= 8 ? 32 : 1)
     for (int c = 0; c <= a; ++c) {
-      double s = 0.0;
+      R s = X[pk(a, a)] * X[pk(a, c)];
 #pragma unroll (n <= 8 ? 32 : 1)
-      for (int k = a; k < n; ++k) s = fma(X[k * n + a], X[k * n + c], s);
-      Cinv[a * n + c] = s;
-      Cinv[c * n + a] = s;
+      for (int k = a + 1; k < n; ++k) s = r_fma(X[pk(k, a)], X[pk(k, c)], s);
+      Cinv[pk(a, c)] = s;
     }
-  return ok;
 }
 
 // Lower Cholesky factor and its inverse of the leading d x d block of a
-// symmetric n x n block (runtime d <= n).  Returns false unless positive.
-template <int n, typename T>
-PGV_DEV bool chol_lead(const double* S, int d, T* L, T* Li) {
-  double l[n * n], x[n * n];
+// symmetric full n x n block (runtime d <= n), as full row-major arrays.
+template <int n, typename R>
+PGV_DEV bool chol_lead(const R* S, int d, R* L, R* Li) {
   bool ok = true;
+  const R zero = r_fromf<R>(0.0f);
+  for (int e = 0; e < n * n; ++e) {
+    L[e] = zero;
+    Li[e] = zero;
+  }
   for (int j = 0; j < d; ++j) {
-    double s = S[j * n + j];
-    for (int k = 0; k < j; ++k) s = fma(-l[j * n + k], l[j * n + k], s);
-    ok = ok && (s > 0.0);
-    s = ok ? s : 1.0;
-    double rs = pgv_rsqrt(s);
-    l[j * n + j] = s * rs;
-    x[j * n + j] = rs;
+    R s = S[j * n + j];
+    for (int k = 0; k < j; ++k) s = r_fma(-L[j * n + k], L[j * n + k], s);
+    ok = ok && r_pos(s);
+    s = r_pos(s) ? s : r_fromf<R>(1.0f);
+    R rs = r_rsqrt(s);
+    L[j * n + j] = s * rs;
+    Li[j * n + j] = rs;
     for (int i = j + 1; i < d; ++i) {
-      double t = S[i * n + j];
-      for (int k = 0; k < j; ++k) t = fma(-l[i * n + k], l[j * n + k], t);
-      l[i * n + j] = t * rs;
+      R t = S[i * n + j];
+      for (int k = 0; k < j; ++k) t = r_fma(-L[i * n + k], L[j * n + k], t);
+      L[i * n + j] = t * rs;
     }
   }
   for (int j = 0; j < d; ++j)
     for (int i = j + 1; i < d; ++i) {
-      double s = 0.0;
-      for (int k = j; k < i; ++k) s = fma(l[i * n + k], x[k * n + j], s);
-      x[i * n + j] = -s * x[i * n + i];
-    }
-  for (int i = 0; i < d; ++i)
-    for (int j = 0; j < d; ++j) {
-      L[i * n + j] = (T)(j <= i ? l[i * n + j] : 0.0);
-      Li[i * n + j] = (T)(j <= i ? x[i * n + j] : 0.0);
+      R s = zero;
+      for (int k = j; k < i; ++k) s = r_fma(L[i * n + k], Li[k * n + j], s);
+      Li[i * n + j] = -(s * Li[i * n + i]);
     }
   return ok;
 }

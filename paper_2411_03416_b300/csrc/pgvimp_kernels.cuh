@@ -1,31 +1,56 @@
-// pgvimp_kernels.cu -- the P-GVIMP hot path on sm_103a, one plan per thread.
+// pgvimp_kernels.cuh -- the P-GVIMP hot path on sm_103a, one plan per thread.
 //
 // Rows of the path and where they live:
-//   prior build (Alg. 1, lines 1-2)         prior_build<n>       / k_prior
-//   marginals by GBP on the chain (Sec. 5.1) marginals<n>        / k_init, k_marginals
-//   factor expectations (Sec. 4.1-4.3)      quad_factor<n, QT>   / k_quad, k_iterate
-//   gradient assembly (Sec. 4.2)            quad_factor<n, QT>
-//   Thm 1 update + step search (App. C)     trial<n>, search<n>  / k_trial, k_iterate
-//   SLR linearisation (Sec. 6.2, Alg. 2)    slr_step<n, QT>      / k_slr
+//   prior build (Alg. 1, lines 1-2)          prior_build<n, R>        / k_prior
+//   marginals on the chain (Sec. 5.1)        marginals<n, R>          / k_init, k_marginals
+//   factor expectations (Sec. 4.1-4.3)       quad_factor<n, QT, R>    / k_quad, k_iterate
+//   gradient assembly (Sec. 4.2)             quad_factor<n, QT, R>
+//   Thm 1 update + step search (App. C)      trial<n, R>, iterate_once / k_trial, k_iterate
+//   SLR linearisation (Sec. 6.2, Alg. 2)     slr_step<n, QT>          / k_slr
 //
-// GBP on a chain is the exact two-pass message schedule; here the forward
-// messages are carried as Schur-complement pivots C_i (the precision of x_i
-// given x_{<i} marginalised), and the backward messages as the covariance
-// recursion Sigma_i = C_i^-1 + W_i^T Sigma_{i+1} W_i, Sigma_{i+1,i} =
-// -Sigma_{i+1} W_i with W_i = Lambda_{i+1,i} C_i^-1.  Both carry only PSD sums
-// in the backward direction, which keeps FP64 accuracy at N ~ 1000.
+// QT is the quadrature arithmetic (float in the mixed forms, double in the
+// plain FP64 form); R the arithmetic and storage of the block recursions
+// (double, or the double-float df64).
+//
+// Gaussian belief propagation on a chain is the exact two-pass schedule; here
+// the forward messages are carried as Schur-complement pivots C_i (the
+// precision of x_i after the states before it are marginalised out) and the
+// backward messages as the covariance recursion
+//   Sigma_i = C_i^-1 + W_i^T Sigma_{i+1} W_i,  Sigma_{i+1,i} = -Sigma_{i+1} W_i,
+// with W_i = Lambda_{i+1,i} C_i^-1.  The backward direction adds only PSD
+// terms, which keeps the marginals accurate at N ~ 1000.
 #pragma once
 #include <cuda_runtime.h>
 #include <math.h>
+
+#include <type_traits>
 
 #include "pgvimp_device.cuh"
 
 namespace pgv {
 
+// Per-state scratch of a sweep (elements of R): packed C_A^-1, W_A, W_M, z.
 template <int n>
-__host__ __device__ constexpr int scr_stride() { return 3 * n * n + n; }
+struct Scr {
+  static constexpr int np = n * (n + 1) / 2;
+  static constexpr int npe = np + (np & 1);
+  static constexpr int oCi = 0, oWA = npe, oWM = npe + n * n, oZ = npe + 2 * n * n;
+  static constexpr int stride = npe + 2 * n * n + n;
+};
 
 PGV_DEV double ln_2pie() { return 2.8378770664093454836; }  // 1 + ln(2 pi)
+
+template <typename R>
+PGV_DEV R* rp(double* p) { return reinterpret_cast<R*>(p); }
+template <typename R>
+PGV_DEV const R* rp(const double* p) { return reinterpret_cast<const R*>(p); }
+
+template <int n, typename R>
+PGV_DEV void st_blk_from_double(R* p, const double* X) {
+  R Y[n * n];
+  for (int e = 0; e < n * n; ++e) Y[e] = r_from<R>(X[e]);
+  st_blk<n, R>(p, Y);
+}
 
 // ------------------------------------------------------------ prior (a0)
 
@@ -72,67 +97,85 @@ PGV_BIG bool van_loan(const double* A, const double* a, const double* Wn, double
   return true;
 }
 
-// Block-tridiagonal solve M x = r (M symmetric positive definite, diagonal
-// blocks Md, lower blocks Mo) by the same forward elimination / back
-// substitution as the trial sweep; scratch from P.scr.
+// Inverse of an SPD n x n block (full, FP64) through the packed Cholesky.
 template <int n>
-PGV_BIG bool bt_solve(const PlanDesc& P, const double* Md, const double* Mo, const double* r, double* x) {
-  constexpr int nn = n * n, SS = scr_stride<n>();
-  const int N = P.N;
-  double S[nn], C[nn], Ci[nn], E[nn], Wm[nn], y[n], yp[n], z[n];
-  LogDetAcc ld;
+PGV_DEV bool spd_inverse_full(const double* A, double* Ai) {
+  constexpr int np = n * (n + 1) / 2;
+  double P[np], Pi[np];
+  for (int a = 0; a < n; ++a)
+    for (int c = 0; c <= a; ++c) P[pk(a, c)] = A[a * n + c];
+  LogDetAcc<double> ld;
   ld.init();
   bool ok = true;
-  for (int e = 0; e < nn; ++e) S[e] = 0.0;
-  for (int a = 0; a < n; ++a) yp[a] = 0.0;
-  for (int e = 0; e < nn; ++e) Wm[e] = 0.0;
+  chol_inverse<n, double>(P, Pi, ld, ok);
+  for (int a = 0; a < n; ++a)
+    for (int c = 0; c < n; ++c) Ai[a * n + c] = Pi[pk(a, c)];
+  return ok;
+}
+
+// Block-tridiagonal SPD solve M x = r (diagonal blocks Md, lower blocks Mo)
+// by forward elimination and back substitution; scratch from P.scr.
+template <int n, typename R>
+PGV_BIG bool bt_solve(const PlanDesc& P, const R* Md, const R* Mo, const R* r, R* x) {
+  constexpr int nn = n * n, np = Scr<n>::np, SS = Scr<n>::stride;
+  const int N = P.N;
+  R* scr = rp<R>(P.scr);
+  R S[np], v[n];
+  const R zero = r_fromf<R>(0.0f);
+  for (int e = 0; e < np; ++e) S[e] = zero;
+  for (int a = 0; a < n; ++a) v[a] = zero;
+  LogDetAcc<R> ld;
+  ld.init();
+  bool ok = true;
   for (int i = 0; i <= N; ++i) {
-    ld_blk<n>(Md + (size_t)i * nn, C);
-    for (int e = 0; e < nn; ++e) C[e] -= S[e];
-    ok = chol_inverse<n>(C, Ci, ld) && ok;
+    R C[np], Ci[np], y[n], z[n];
+    ld_sym<n, R>(Md + (size_t)i * nn, C);
+    for (int e = 0; e < np; ++e) C[e] = C[e] - S[e];
+    chol_inverse<n, R>(C, Ci, ld, ok);
+    for (int a = 0; a < n; ++a) y[a] = r[(size_t)i * n + a] - v[a];
     for (int a = 0; a < n; ++a) {
-      double s = r[(size_t)i * n + a];
-      for (int c = 0; c < n; ++c) s = fma(-Wm[a * n + c], yp[c], s);
-      y[a] = s;
-    }
-    for (int a = 0; a < n; ++a) {
-      double s = 0.0;
-      for (int c = 0; c < n; ++c) s = fma(Ci[a * n + c], y[c], s);
+      R s = Ci[pk(a, 0)] * y[0];
+      for (int c = 1; c < n; ++c) s = r_fma(Ci[pk(a, c)], y[c], s);
       z[a] = s;
     }
-    double* sp = P.scr + (size_t)i * SS;
-    st_vec<n>(sp + 3 * nn, z);
+    R* sp = scr + (size_t)i * SS;
+    st_vec<n, R>(sp + Scr<n>::oZ, z);
     if (i < N) {
-      ld_blk<n>(Mo + (size_t)i * nn, E);
-      mul_nn<n>(E, Ci, Wm);
-      mul_nt_sym<n>(Wm, E, S);
-      st_blk<n>(sp + nn, Wm);
+      R E[nn], W[nn];
+      ld_blk<n, R>(Mo + (size_t)i * nn, E);
+      mul_full_sym<n, R>(E, Ci, W);
+      mul_nt_packed<n, R>(W, E, S);
+      for (int a = 0; a < n; ++a) {
+        R s = W[a * n] * y[0];
+        for (int c = 1; c < n; ++c) s = r_fma(W[a * n + c], y[c], s);
+        v[a] = s;
+      }
+      st_blk<n, R>(sp + Scr<n>::oWA, W);
     }
-    for (int a = 0; a < n; ++a) yp[a] = y[a];
   }
-  double xn[n];
-  ld_vec<n>(P.scr + (size_t)N * SS + 3 * nn, xn);
-  st_vec<n>(x + (size_t)N * n, xn);
+  R xn[n];
+  ld_vec<n, R>(scr + (size_t)N * SS + Scr<n>::oZ, xn);
+  st_vec<n, R>(x + (size_t)N * n, xn);
   for (int i = N - 1; i >= 0; --i) {
-    const double* sp = P.scr + (size_t)i * SS;
-    ld_blk<n>(sp + nn, Wm);
-    ld_vec<n>(sp + 3 * nn, z);
-    double xi[n];
+    const R* sp = scr + (size_t)i * SS;
+    R W[nn], z[n], xi[n];
+    ld_blk<n, R>(sp + Scr<n>::oWA, W);
+    ld_vec<n, R>(sp + Scr<n>::oZ, z);
     for (int a = 0; a < n; ++a) {
-      double s = z[a];
-      for (int c = 0; c < n; ++c) s = fma(-Wm[c * n + a], xn[c], s);
+      R s = z[a];
+      for (int c = 0; c < n; ++c) s = r_fma(-W[c * n + a], xn[c], s);
       xi[a] = s;
     }
-    st_vec<n>(x + (size_t)i * n, xi);
+    st_vec<n, R>(x + (size_t)i * n, xi);
     for (int a = 0; a < n; ++a) xn[a] = xi[a];
   }
   return ok;
 }
 
 // Prior precision K^-1 (block tridiagonal), information vector b = K^-1 mu_bar
-// and mu_bar itself, for the LTI / LTV system given by (A, a) or, when Altv
-// is non-null, by the SLR linearisation (Altv, altv).
-template <int n>
+// and mu_bar, for the LTI / LTV system given by (A, a) or, with `use_ltv`, by
+// the SLR linearisation (Altv, altv).  FP64 throughout; stored as R.
+template <int n, typename R>
 PGV_BIG bool prior_build(const PlanDesc& P, bool use_ltv) {
   constexpr int nn = n * n;
   const int N = P.N, m = P.m;
@@ -146,15 +189,13 @@ PGV_BIG bool prior_build(const PlanDesc& P, bool use_ltv) {
     }
   const bool lti = !use_ltv && !P.A_per_step && !P.a_per_step;
   double carry_d[nn], carry_b[n], PtQi[nn], T1[nn];
-  LogDetAcc dummy;
-  dummy.init();
   bool ok = true;
-  // start factor
+  R* Kd = rp<R>(P.Kd);
+  R* Ko = rp<R>(P.Ko);
+  R* b = rp<R>(P.b);
   {
     double K0i[nn];
-    double K0[nn];
-    for (int e = 0; e < nn; ++e) K0[e] = P.K0[e];
-    ok = chol_inverse<n>(K0, K0i, dummy) && ok;
+    ok = spd_inverse_full<n>(P.K0, K0i) && ok;
     for (int e = 0; e < nn; ++e) carry_d[e] = K0i[e];
     for (int a = 0; a < n; ++a) {
       double s = 0.0;
@@ -170,8 +211,7 @@ PGV_BIG bool prior_build(const PlanDesc& P, bool use_ltv) {
       for (int a = 0; a < n; ++a)
         av[a] = use_ltv ? P.altv[(size_t)i * n + a] : (P.a ? (P.a_per_step ? P.a[(size_t)i * n + a] : P.a[a]) : 0.0);
       ok = van_loan<n>(A, av, Wn, P.dt, Phi, Q, u) && ok;
-      ok = chol_inverse<n>(Q, Qi, dummy) && ok;
-      // PtQi = Phi^T Q^-1
+      ok = spd_inverse_full<n>(Q, Qi) && ok;
       for (int r = 0; r < n; ++r)
         for (int c = 0; c < n; ++c) {
           double s = 0.0;
@@ -180,8 +220,13 @@ PGV_BIG bool prior_build(const PlanDesc& P, bool use_ltv) {
         }
     }
     // K^-1_ii = carry + Phi^T Q^-1 Phi ; b_i = carry_b - Phi^T Q^-1 u
-    mul_nn<n>(PtQi, Phi, T1);
     double blk[nn], bv[n];
+    for (int r = 0; r < n; ++r)
+      for (int c = 0; c < n; ++c) {
+        double s = 0.0;
+        for (int k = 0; k < n; ++k) s = fma(PtQi[r * n + k], Phi[k * n + c], s);
+        T1[r * n + c] = s;
+      }
     for (int e = 0; e < nn; ++e) blk[e] = (carry_d[e] + T1[e]) * it;
     for (int r = 0; r < n; ++r)
       for (int c = 0; c < r; ++c) {
@@ -189,17 +234,21 @@ PGV_BIG bool prior_build(const PlanDesc& P, bool use_ltv) {
         blk[r * n + c] = s;
         blk[c * n + r] = s;
       }
-    st_blk<n>(P.Kd + (size_t)i * nn, blk);
+    st_blk_from_double<n, R>(Kd + (size_t)i * nn, blk);
     for (int a = 0; a < n; ++a) {
       double s = carry_b[a];
       for (int c = 0; c < n; ++c) s = fma(-PtQi[a * n + c], u[c], s);
       bv[a] = s * it;
     }
-    st_vec<n>(P.b + (size_t)i * n, bv);
+    for (int a = 0; a < n; ++a) b[(size_t)i * n + a] = r_from<R>(bv[a]);
     // K^-1_{i+1,i} = -Q^-1 Phi
-    mul_nn<n>(Qi, Phi, T1);
-    for (int e = 0; e < nn; ++e) blk[e] = -T1[e] * it;
-    st_blk<n>(P.Ko + (size_t)i * nn, blk);
+    for (int r = 0; r < n; ++r)
+      for (int c = 0; c < n; ++c) {
+        double s = 0.0;
+        for (int k = 0; k < n; ++k) s = fma(Qi[r * n + k], Phi[k * n + c], s);
+        blk[r * n + c] = -s * it;
+      }
+    st_blk_from_double<n, R>(Ko + (size_t)i * nn, blk);
     for (int e = 0; e < nn; ++e) carry_d[e] = Qi[e];
     for (int a = 0; a < n; ++a) {
       double s = 0.0;
@@ -208,110 +257,134 @@ PGV_BIG bool prior_build(const PlanDesc& P, bool use_ltv) {
     }
   }
   {
-    double KN[nn], KNi[nn], blk[nn], bv[n];
-    for (int e = 0; e < nn; ++e) KN[e] = P.KN[e];
-    ok = chol_inverse<n>(KN, KNi, dummy) && ok;
+    double KNi[nn], blk[nn];
+    ok = spd_inverse_full<n>(P.KN, KNi) && ok;
     for (int e = 0; e < nn; ++e) blk[e] = (carry_d[e] + KNi[e]) * it;
-    st_blk<n>(P.Kd + (size_t)N * nn, blk);
+    st_blk_from_double<n, R>(Kd + (size_t)N * nn, blk);
     for (int a = 0; a < n; ++a) {
       double s = carry_b[a];
       for (int c = 0; c < n; ++c) s = fma(KNi[a * n + c], P.muN[c], s);
-      bv[a] = s * it;
+      b[(size_t)N * n + a] = r_from<R>(s * it);
     }
-    st_vec<n>(P.b + (size_t)N * n, bv);
   }
-  if (ok) ok = bt_solve<n>(P, P.Kd, P.Ko, P.b, P.mubar);
+  if (ok) ok = bt_solve<n, R>(P, Kd, Ko, b, rp<R>(P.mubar));
   return ok;
 }
 
 // ------------------------------------------------------------ marginals (a1)
 
-// Marginal blocks of the block-tridiagonal precision (Ld, Lo) into set s, the
-// log det, and the prior cost 1/2[tr(K^-1 Sigma) + (mu-mubar)^T K^-1 (mu-mubar)]
-// of the iterate (mu[s], Sigma).
-template <int n>
-PGV_BIG bool marginals(const PlanDesc& P, const double* Ld, const double* Lo, int s, double& logdet,
-                       double& prior_cost) {
-  constexpr int nn = n * n, SS = scr_stride<n>();
+// Marginal blocks of the precision (Ld, Lo) into buffer set s, log det, and
+// the prior cost 1/2 [tr(K^-1 Sigma) + (mu - mubar)^T K^-1 (mu - mubar)] of
+// the iterate (mu[s], Sigma).
+template <int n, typename R>
+PGV_BIG bool marginals(const PlanDesc& P, int s, double& logdet, double& prior_cost) {
+  constexpr int nn = n * n, np = Scr<n>::np, SS = Scr<n>::stride;
   const int N = P.N;
-  double S[nn], C[nn], Ci[nn], E[nn], W[nn];
-  LogDetAcc ld;
+  const R* Ld = rp<R>(P.Ld);
+  const R* Lo = rp<R>(P.Lo);
+  const R* Kd = rp<R>(P.Kd);
+  const R* Ko = rp<R>(P.Ko);
+  const R* mubar = rp<R>(P.mubar);
+  const R* mu = rp<R>(P.mu[s]);
+  R* Sd = rp<R>(P.Sd[s]);
+  R* So = rp<R>(P.So[s]);
+  R* scr = rp<R>(P.scr);
+  R S[np];
+  const R zero = r_fromf<R>(0.0f);
+  for (int e = 0; e < np; ++e) S[e] = zero;
+  LogDetAcc<R> ld;
   ld.init();
   bool ok = true;
-  for (int e = 0; e < nn; ++e) S[e] = 0.0;
   for (int i = 0; i <= N; ++i) {
-    ld_blk<n>(Ld + (size_t)i * nn, C);
-    for (int e = 0; e < nn; ++e) C[e] -= S[e];
-    ok = chol_inverse<n>(C, Ci, ld) && ok;
-    double* sp = P.scr + (size_t)i * SS;
-    st_blk<n>(sp, Ci);
+    R C[np], Ci[np];
+    ld_sym<n, R>(Ld + (size_t)i * nn, C);
+    for (int e = 0; e < np; ++e) C[e] = C[e] - S[e];
+    chol_inverse<n, R>(C, Ci, ld, ok);
+    R* sp = scr + (size_t)i * SS;
+    st_packed<n, R>(sp + Scr<n>::oCi, Ci);
     if (i < N) {
-      ld_blk<n>(Lo + (size_t)i * nn, E);
-      mul_nn<n>(E, Ci, W);
-      mul_nt_sym<n>(W, E, S);
-      st_blk<n>(sp + nn, W);
+      R E[nn], W[nn];
+      ld_blk<n, R>(Lo + (size_t)i * nn, E);
+      mul_full_sym<n, R>(E, Ci, W);
+      mul_nt_packed<n, R>(W, E, S);
+      st_blk<n, R>(sp + Scr<n>::oWA, W);
     }
   }
   logdet = ld.log_value();
   if (!ok) return false;
-  double Sn[nn], T[nn], Si[nn], K[nn], dn[n], di[n];
-  const double* mu = P.mu[s];
-  ld_blk<n>(P.scr + (size_t)N * SS, Sn);
-  st_blk<n>(P.Sd[s] + (size_t)N * nn, Sn);
-  double tr = 0.0, qd = 0.0;
-  ld_blk<n>(P.Kd + (size_t)N * nn, K);
-  for (int a = 0; a < n; ++a) dn[a] = mu[(size_t)N * n + a] - P.mubar[(size_t)N * n + a];
-  for (int e = 0; e < nn; ++e) tr = fma(K[e], Sn[e], tr);
-  for (int a = 0; a < n; ++a)
-    for (int c = 0; c < n; ++c) qd = fma(dn[a] * K[a * n + c], dn[c], qd);
-  for (int i = N - 1; i >= 0; --i) {
-    const double* sp = P.scr + (size_t)i * SS;
-    ld_blk<n>(sp, Ci);
-    ld_blk<n>(sp + nn, W);
-    mul_nn<n>(Sn, W, T);
-    add_tn_sym<n>(Ci, W, T, Si);
-    for (int e = 0; e < nn; ++e) T[e] = -T[e];
-    st_blk<n>(P.So[s] + (size_t)i * nn, T);
-    st_blk<n>(P.Sd[s] + (size_t)i * nn, Si);
-    ld_blk<n>(P.Kd + (size_t)i * nn, K);
-    ld_blk<n>(P.Ko + (size_t)i * nn, E);
-    for (int a = 0; a < n; ++a) di[a] = mu[(size_t)i * n + a] - P.mubar[(size_t)i * n + a];
-    for (int e = 0; e < nn; ++e) tr = fma(K[e], Si[e], fma(2.0 * E[e], T[e], tr));
+  R Sn[np], dn[n];
+  ld_packed<n, R>(scr + (size_t)N * SS + Scr<n>::oCi, Sn);
+  st_sym<n, R>(Sd + (size_t)N * nn, Sn);
+  R tr = zero, qd = zero;
+  {
+    R K[nn];
+    ld_blk<n, R>(Kd + (size_t)N * nn, K);
+    for (int a = 0; a < n; ++a) dn[a] = mu[(size_t)N * n + a] - mubar[(size_t)N * n + a];
     for (int a = 0; a < n; ++a)
       for (int c = 0; c < n; ++c) {
-        qd = fma(di[a] * K[a * n + c], di[c], qd);
-        qd = fma(2.0 * dn[a] * E[a * n + c], di[c], qd);
+        tr = r_fma(K[a * n + c], Sn[pk(a, c)], tr);
+        qd = r_fma(dn[a] * K[a * n + c], dn[c], qd);
       }
-    for (int e = 0; e < nn; ++e) Sn[e] = Si[e];
+  }
+  for (int i = N - 1; i >= 0; --i) {
+    const R* sp = scr + (size_t)i * SS;
+    R Ci[np], W[nn], T[nn], Si[np], di[n];
+    ld_packed<n, R>(sp + Scr<n>::oCi, Ci);
+    ld_blk<n, R>(sp + Scr<n>::oWA, W);
+    mul_sym_full<n, R>(Sn, W, T);           // Sigma_{i+1} W_i = -Sigma_{i+1,i}
+    add_tn_packed<n, R>(Ci, W, T, Si);
+    for (int e = 0; e < nn; ++e) T[e] = -T[e];
+    st_blk<n, R>(So + (size_t)i * nn, T);
+    st_sym<n, R>(Sd + (size_t)i * nn, Si);
+    R K[nn], E[nn];
+    ld_blk<n, R>(Kd + (size_t)i * nn, K);
+    ld_blk<n, R>(Ko + (size_t)i * nn, E);
+    for (int a = 0; a < n; ++a) di[a] = mu[(size_t)i * n + a] - mubar[(size_t)i * n + a];
+    for (int a = 0; a < n; ++a)
+      for (int c = 0; c < n; ++c) {
+        tr = r_fma(K[a * n + c], Si[pk(a, c)], tr);
+        tr = r_fma(E[a * n + c] + E[a * n + c], T[a * n + c], tr);
+        qd = r_fma(di[a] * K[a * n + c], di[c], qd);
+        qd = r_fma((dn[a] + dn[a]) * E[a * n + c], di[c], qd);
+      }
+    for (int e = 0; e < np; ++e) Sn[e] = Si[e];
     for (int a = 0; a < n; ++a) dn[a] = di[a];
   }
-  prior_cost = 0.5 * (tr + qd);
+  prior_cost = 0.5 * r_to(tr + qd);
   return true;
 }
 
-// Prior cost of the iterate in set s (used after a relinearisation changes K^-1).
-template <int n>
+// Prior cost of the iterate in set s (after a relinearisation changes K^-1).
+template <int n, typename R>
 PGV_BIG double prior_cost_of(const PlanDesc& P, int s) {
   constexpr int nn = n * n;
   const int N = P.N;
-  double tr = 0.0, qd = 0.0, K[nn], E[nn], Sb[nn], Ob[nn], di[n], dn[n];
+  const R* Kd = rp<R>(P.Kd);
+  const R* Ko = rp<R>(P.Ko);
+  const R* mu = rp<R>(P.mu[s]);
+  const R* mubar = rp<R>(P.mubar);
+  const R* Sd = rp<R>(P.Sd[s]);
+  const R* So = rp<R>(P.So[s]);
+  R tr = r_fromf<R>(0.0f), qd = r_fromf<R>(0.0f), di[n], dn[n];
   for (int i = N; i >= 0; --i) {
-    ld_blk<n>(P.Kd + (size_t)i * nn, K);
-    ld_blk<n>(P.Sd[s] + (size_t)i * nn, Sb);
-    for (int a = 0; a < n; ++a) di[a] = P.mu[s][(size_t)i * n + a] - P.mubar[(size_t)i * n + a];
-    for (int e = 0; e < nn; ++e) tr = fma(K[e], Sb[e], tr);
+    R K[nn], Sb[nn];
+    ld_blk<n, R>(Kd + (size_t)i * nn, K);
+    ld_blk<n, R>(Sd + (size_t)i * nn, Sb);
+    for (int a = 0; a < n; ++a) di[a] = mu[(size_t)i * n + a] - mubar[(size_t)i * n + a];
+    for (int e = 0; e < nn; ++e) tr = r_fma(K[e], Sb[e], tr);
     for (int a = 0; a < n; ++a)
-      for (int c = 0; c < n; ++c) qd = fma(di[a] * K[a * n + c], di[c], qd);
+      for (int c = 0; c < n; ++c) qd = r_fma(di[a] * K[a * n + c], di[c], qd);
     if (i < N) {
-      ld_blk<n>(P.Ko + (size_t)i * nn, E);
-      ld_blk<n>(P.So[s] + (size_t)i * nn, Ob);
-      for (int e = 0; e < nn; ++e) tr = fma(2.0 * E[e], Ob[e], tr);
+      R E[nn], Ob[nn];
+      ld_blk<n, R>(Ko + (size_t)i * nn, E);
+      ld_blk<n, R>(So + (size_t)i * nn, Ob);
+      for (int e = 0; e < nn; ++e) tr = r_fma(E[e] + E[e], Ob[e], tr);
       for (int a = 0; a < n; ++a)
-        for (int c = 0; c < n; ++c) qd = fma(2.0 * dn[a] * E[a * n + c], di[c], qd);
+        for (int c = 0; c < n; ++c) qd = r_fma((dn[a] + dn[a]) * E[a * n + c], di[c], qd);
     }
     for (int a = 0; a < n; ++a) dn[a] = di[a];
   }
-  return 0.5 * (tr + qd);
+  return 0.5 * r_to(tr + qd);
 }
 
 // ------------------------------------------------------- quadrature (a2-a4)
@@ -330,46 +403,56 @@ PGV_DEV QT point_psi(const PlanDesc& P, const int* gb, const QT* gf, const QT* d
                     gf[2] + dx[2] * ic);
     return hinge_psi<QT>(P, (QT)P.eps - s);
   }
-  // arm: joint angles
   QT q[kMaxDof];
   for (int a = 0; a < P.arm_dof; ++a) q[a] = mu_a[a] + dx[a];
   return arm_cost<QT>(P, q);
+}
+
+// Grid coordinate (mu - origin)/cell split into an exact integer part and a
+// fraction, evaluated in the recursion's arithmetic.
+template <typename QT>
+PGV_DEV void grid_split(double mu, double origin, double inv_cell, int& base, QT& frac) {
+  double u = (mu - origin) * inv_cell;
+  double fl = floor(u);
+  base = (int)fl;
+  frac = (QT)(u - fl);
+}
+template <typename QT>
+PGV_DEV void grid_split(df64 mu, double origin, double inv_cell, int& base, QT& frac) {
+  df64 u = (mu - r_from<df64>(origin)) * r_from<df64>(inv_cell);
+  float fl = floorf(u.hi);
+  base = (int)fl;
+  frac = (QT)((u.hi - fl) + u.lo);
 }
 
 // E[psi_i] and the gradients g_i = Sigma^-1 E[(x-mu) psi],
 // G_i = -1/2 Sigma^-1 E[psi] + 1/2 Sigma^-1 E[(x-mu)(x-mu)^T psi] Sigma^-1
 // (Sec. 4.1 moment form) for one factor.  With x = mu + L xi and L lower
 // triangular, the cost (a function of the leading dc coordinates) depends on
-// xi_0..xi_{dc-1} only, so the quadrature runs over the dc-dimensional rule
-// in xi-space: g = L^-T E[xi psi], G = 1/2 L^-T (E[xi xi^T psi] - E[psi] I) L^-1,
-// where the trailing moments are known in closed form (tensor GH: xi_b
-// independent of psi; degree 3: +-sqrt(3) e_b points evaluate psi(mu)).
-template <int n, typename QT>
-PGV_DEV bool quad_factor(const PlanDesc& P, int i, const double* mu_i, const double* S_ii, double* g,
-                         double* G, double& M0_out) {
+// xi_0..xi_{dc-1} only, so the quadrature runs over the dc-dimensional rule in
+// xi-space: g = L^-T E[xi psi], G = 1/2 L^-T (E[xi xi^T psi] - E[psi] I) L^-1,
+// the trailing moments being known in closed form (tensor GH: xi_b is
+// independent of psi; degree 3: the +-sqrt(3) e_b points evaluate psi(mu)).
+template <int n, typename QT, typename R>
+PGV_DEV bool quad_factor(const PlanDesc& P, int i, const R* mu_i, const R* S_ii, R* g, R* G, double& M0_out) {
   constexpr int nn = n * n;
-  for (int a = 0; a < n; ++a) g[a] = 0.0;
-  for (int e = 0; e < nn; ++e) G[e] = 0.0;
+  const R zero = r_fromf<R>(0.0f);
+  for (int a = 0; a < n; ++a) g[a] = zero;
+  for (int e = 0; e < nn; ++e) G[e] = zero;
   M0_out = 0.0;
   if (P.cost_kind == PGVIMP_COST_NONE || (P.factor_set == 1 && (i == 0 || i == P.N))) return true;
   const int dc = P.dc;
   const bool deg3 = (P.rule == PGVIMP_RULE_DEG3);
   const int dL = deg3 ? n : dc;
-  double L[nn], Li[nn];
-  if (!chol_lead<n, double>(S_ii, dL, L, Li)) return false;
+  R L[nn], Li[nn];
+  if (!chol_lead<n, R>(S_ii, dL, L, Li)) return false;
   QT Lq[nn], mua[kMaxN];
-  for (int e = 0; e < nn; ++e) Lq[e] = (QT)L[e];
-  for (int a = 0; a < dc; ++a) mua[a] = (QT)mu_i[a];
+  for (int e = 0; e < nn; ++e) Lq[e] = (QT)r_to(L[e]);
+  for (int a = 0; a < dc; ++a) mua[a] = (QT)r_to(mu_i[a]);
   int gb[3] = {0, 0, 0};
   QT gf[3] = {0, 0, 0};
-  if (P.cost_kind != PGVIMP_COST_ARM) {
-    for (int a = 0; a < dc; ++a) {
-      double u = (mu_i[a] - P.sdf_origin[a]) * P.inv_cell;
-      double fl = floor(u);
-      gb[a] = (int)fl;
-      gf[a] = (QT)(u - fl);
-    }
-  }
+  if (P.cost_kind != PGVIMP_COST_ARM)
+    for (int a = 0; a < dc; ++a) grid_split<QT>(mu_i[a], P.sdf_origin[a], P.inv_cell, gb[a], gf[a]);
   QT M0 = 0, M1[kMaxN], M2[kMaxN * kMaxN];
   for (int a = 0; a < dc; ++a) M1[a] = 0;
   for (int e = 0; e < dc * dc; ++e) M2[e] = 0;
@@ -416,58 +499,64 @@ PGV_DEV bool quad_factor(const PlanDesc& P, int i, const double* mu_i, const dou
       M2[j * dc + j] = (QT)0.5 * (pp + pm);
     }
   }
-  // gradient assembly in FP64: D = blockdiag(M2 - M0 I, (psi_c - M0) I [deg3 only])
-  // (the cost is divided by the temperature T-hat)
+  // gradient assembly: D = blockdiag(M2 - M0 I, (psi_c - M0) I [degree 3 only]);
+  // the cost is divided by the temperature T-hat
   const double it = P.inv_temp;
-  double D[nn];
-  for (int e = 0; e < nn; ++e) D[e] = 0.0;
+  R D[nn];
+  for (int e = 0; e < nn; ++e) D[e] = zero;
   const double m0 = (double)M0 * it;
+  const R m0r = r_from<R>(m0);
   for (int a = 0; a < dc; ++a)
     for (int c = 0; c <= a; ++c) {
-      double v = (double)M2[a * dc + c] * it - (a == c ? m0 : 0.0);
+      R v = r_from<R>((double)M2[a * dc + c] * it);
+      if (a == c) v = v - m0r;
       D[a * n + c] = v;
       D[c * n + a] = v;
     }
   if (deg3)
-    for (int b = dc; b < n; ++b) D[b * n + b] = (double)psi_c * it - m0;
-  // g = Li^T m1
+    for (int b = dc; b < n; ++b) D[b * n + b] = r_from<R>((double)psi_c * it) - m0r;
   for (int r = 0; r < dL; ++r) {
-    double s = 0.0;
-    for (int a = r; a < dc; ++a) s = fma(Li[a * n + r], (double)M1[a] * it, s);
+    R s = zero;
+    for (int a = r; a < dc; ++a) s = r_fma(Li[a * n + r], r_from<R>((double)M1[a] * it), s);
     g[r] = s;
   }
-  // G = 1/2 Li^T D Li  (Li lower triangular, dL x dL)
-  double T[nn];
+  R T[nn];
   for (int a = 0; a < dL; ++a)
     for (int c = 0; c < dL; ++c) {
-      double s = 0.0;
-      for (int b = c; b < dL; ++b) s = fma(D[a * n + b], Li[b * n + c], s);
+      R s = zero;
+      for (int b = c; b < dL; ++b) s = r_fma(D[a * n + b], Li[b * n + c], s);
       T[a * n + c] = s;
     }
+  const R half = r_fromf<R>(0.5f);
   for (int r = 0; r < dL; ++r)
     for (int c = 0; c <= r; ++c) {
-      double s = 0.0;
-      for (int a = r; a < dL; ++a) s = fma(Li[a * n + r], T[a * n + c], s);
-      G[r * n + c] = 0.5 * s;
-      G[c * n + r] = 0.5 * s;
+      R s = zero;
+      for (int a = r; a < dL; ++a) s = r_fma(Li[a * n + r], T[a * n + c], s);
+      G[r * n + c] = half * s;
+      G[c * n + r] = half * s;
     }
   M0_out = m0;
   return true;
 }
 
-template <int n, typename QT>
+template <int n, typename QT, typename R>
 PGV_BIG bool quad_all(const PlanDesc& P, int s, double& coll) {
   constexpr int nn = n * n;
   const int N = P.N;
-  double mu_i[n], S_ii[nn], g[n], G[nn], m0;
+  const R* mu = rp<R>(P.mu[s]);
+  const R* Sd = rp<R>(P.Sd[s]);
+  R* gg = rp<R>(P.g);
+  R* GG = rp<R>(P.G);
   coll = 0.0;
   bool ok = true;
   for (int i = 0; i <= N; ++i) {
-    ld_vec<n>(P.mu[s] + (size_t)i * n, mu_i);
-    ld_blk<n>(P.Sd[s] + (size_t)i * nn, S_ii);
-    ok = quad_factor<n, QT>(P, i, mu_i, S_ii, g, G, m0) && ok;
-    st_vec<n>(P.g + (size_t)i * n, g);
-    st_blk<n>(P.G + (size_t)i * nn, G);
+    R mu_i[n], S_ii[nn], g[n], G[nn];
+    double m0;
+    ld_vec<n, R>(mu + (size_t)i * n, mu_i);
+    ld_blk<n, R>(Sd + (size_t)i * nn, S_ii);
+    ok = quad_factor<n, QT, R>(P, i, mu_i, S_ii, g, G, m0) && ok;
+    st_vec<n, R>(gg + (size_t)i * n, g);
+    st_blk<n, R>(GG + (size_t)i * nn, G);
     coll += m0;
   }
   return ok;
@@ -484,240 +573,321 @@ struct TrialOut {
 //   A~ = beta (2G + K^-1) + Lambda_k          = (beta+1) Lambda'
 //   M  = beta K^-1 + Lambda_k                 (mean system times beta)
 //   M delta = beta (-g + b - K^-1 mu_k),      mu' = mu_k + delta
-// One forward sweep eliminates A~ and M together (they share the
-// off-diagonal blocks); one backward sweep produces Sigma~ = A~^-1 (selected
-// blocks), delta, and the KL pieces
+// One forward sweep eliminates A~ and M together (they share the off-diagonal
+// blocks); one backward sweep produces Sigma~ = A~^-1 (selected blocks), delta
+// and the KL pieces
 //   KL = 1/2 [beta tr((Lambda_k - 2G - K^-1) Sigma~) + delta^T Lambda_k delta
 //             + log det Lambda' - log det Lambda_k],
-// using tr(Lambda_k Sigma') - D = tr((Lambda_k - Lambda') Sigma').
-// Results go to buffer set `out`: mu', Sigma' = (beta+1) Sigma~.
-template <int n>
-PGV_BIG TrialOut trial(const PlanDesc& P, double beta, int cur, int out, double logdet_k) {
-  constexpr int nn = n * n, SS = scr_stride<n>();
+// using tr(Lambda_k Sigma') - D = tr((Lambda_k - Lambda') Sigma').  Results go
+// to buffer set `out`: mu', Sigma' = (beta+1) Sigma~.  Carried between states:
+// the packed Schur terms of both eliminations, W^M_{i-1} y_{i-1} and
+// K^-1_{i,i-1} mu_{i-1} (vectors), not the matrices.
+template <int n, typename R>
+PGV_BIG TrialOut trial(const PlanDesc& P, double beta_d, int cur, int out, double logdet_k) {
+  constexpr int nn = n * n, np = Scr<n>::np, SS = Scr<n>::stride;
   const int N = P.N;
-  const double* mu = P.mu[cur];
-  TrialOut R;
-  R.kl = INFINITY;
-  R.pd = false;
-  R.logdet = 0.0;
-  R.prior_cost = 0.0;
-  R.delta = 0.0;
-  R.trace = 0.0;
-  double SA[nn], SM[nn], WMp[nn], yp[n];
-  for (int e = 0; e < nn; ++e) { SA[e] = 0.0; SM[e] = 0.0; WMp[e] = 0.0; }
-  for (int a = 0; a < n; ++a) yp[a] = 0.0;
-  LogDetAcc ldA, ldM;
+  const R* mu = rp<R>(P.mu[cur]);
+  const R* Kd = rp<R>(P.Kd);
+  const R* Ko = rp<R>(P.Ko);
+  const R* Ld = rp<R>(P.Ld);
+  const R* Lo = rp<R>(P.Lo);
+  const R* GG = rp<R>(P.G);
+  const R* gg = rp<R>(P.g);
+  const R* bb = rp<R>(P.b);
+  const R* mubar = rp<R>(P.mubar);
+  R* scr = rp<R>(P.scr);
+  TrialOut res;
+  res.kl = INFINITY;
+  res.pd = false;
+  res.logdet = 0.0;
+  res.prior_cost = 0.0;
+  res.delta = 0.0;
+  res.trace = 0.0;
+  const R beta = r_from<R>(beta_d), beta2 = beta + beta, zero = r_fromf<R>(0.0f);
+  R SA[np], SM[np], vM[n], q[n], mi[n];
+#pragma unroll (n <= 8 ? 32 : 1)
+  for (int e = 0; e < np; ++e) {
+    SA[e] = zero;
+    SM[e] = zero;
+  }
+#pragma unroll (n <= 8 ? 32 : 1)
+  for (int a = 0; a < n; ++a) {
+    vM[a] = zero;
+    q[a] = zero;
+  }
+  ld_vec<n, R>(mu, mi);
+  LogDetAcc<R> ldA, ldM;
   ldA.init();
   ldM.init();
   bool okA = true, okM = true;
-  double mprev[n], mi[n], mnext[n];
-  for (int a = 0; a < n; ++a) mprev[a] = 0.0;
-  ld_vec<n>(mu, mi);
   for (int i = 0; i <= N; ++i) {
-    double Kd[nn], Lb[nn], Gb[nn], CA[nn], CM[nn], CiA[nn], CiM[nn];
-    ld_blk<n>(P.Kd + (size_t)i * nn, Kd);
-    ld_blk<n>(P.Ld + (size_t)i * nn, Lb);
-    ld_blk<n>(P.G + (size_t)i * nn, Gb);
+    R CA[np], CM[np], Kmu[n];
+    {
+      R B[nn];
+      ld_blk<n, R>(Kd + (size_t)i * nn, B);
 #pragma unroll (n <= 8 ? 32 : 1)
-    for (int e = 0; e < nn; ++e) {
-      double kb = beta * Kd[e];
-      CM[e] = kb + Lb[e] - SM[e];
-      CA[e] = fma(2.0 * beta, Gb[e], kb) + Lb[e] - SA[e];
-    }
-    okA = chol_inverse<n>(CA, CiA, ldA) && okA;
-    okM = chol_inverse<n>(CM, CiM, ldM) && okM;
-    // r_i = beta (-g_i + b_i - (K^-1 mu)_i)
-    double Kmu[n];
-    if (i < N) ld_vec<n>(mu + (size_t)(i + 1) * n, mnext);
+      for (int a = 0; a < n; ++a) {
+        R s = q[a];
 #pragma unroll (n <= 8 ? 32 : 1)
-    for (int a = 0; a < n; ++a) {
-      double s = 0.0;
-#pragma unroll (n <= 8 ? 32 : 1)
-      for (int c = 0; c < n; ++c) s = fma(Kd[a * n + c], mi[c], s);
-      Kmu[a] = s;
-    }
-    if (i > 0) {
-      double Eo[nn];
-      ld_blk<n>(P.Ko + (size_t)(i - 1) * nn, Eo);
+        for (int c = 0; c < n; ++c) s = r_fma(B[a * n + c], mi[c], s);
+        Kmu[a] = s;
+      }
 #pragma unroll (n <= 8 ? 32 : 1)
       for (int a = 0; a < n; ++a)
 #pragma unroll (n <= 8 ? 32 : 1)
-        for (int c = 0; c < n; ++c) Kmu[a] = fma(Eo[a * n + c], mprev[c], Kmu[a]);
+        for (int c = 0; c <= a; ++c) {
+          R kb = beta * B[a * n + c];
+          CM[pk(a, c)] = kb - SM[pk(a, c)];
+          CA[pk(a, c)] = kb - SA[pk(a, c)];
+        }
+      ld_blk<n, R>(GG + (size_t)i * nn, B);
+#pragma unroll (n <= 8 ? 32 : 1)
+      for (int a = 0; a < n; ++a)
+#pragma unroll (n <= 8 ? 32 : 1)
+        for (int c = 0; c <= a; ++c) CA[pk(a, c)] = r_fma(beta2, B[a * n + c], CA[pk(a, c)]);
+      ld_blk<n, R>(Ld + (size_t)i * nn, B);
+#pragma unroll (n <= 8 ? 32 : 1)
+      for (int a = 0; a < n; ++a)
+#pragma unroll (n <= 8 ? 32 : 1)
+        for (int c = 0; c <= a; ++c) {
+          CA[pk(a, c)] = CA[pk(a, c)] + B[a * n + c];
+          CM[pk(a, c)] = CM[pk(a, c)] + B[a * n + c];
+        }
     }
-    double En[nn], Kon[nn];
+    R CiA[np], CiM[np];
+    chol_inverse<n, R>(CA, CiA, ldA, okA);
+    chol_inverse<n, R>(CM, CiM, ldM, okM);
+    R E[nn], mnext[n];
     if (i < N) {
-      ld_blk<n>(P.Ko + (size_t)i * nn, Kon);
-      ld_blk<n>(P.Lo + (size_t)i * nn, En);
+      ld_vec<n, R>(mu + (size_t)(i + 1) * n, mnext);
+      ld_blk<n, R>(Ko + (size_t)i * nn, E);
+      // K^-1 mu at i gets K^-1_{i,i+1} mu_{i+1}; at i+1 it gets K^-1_{i+1,i} mu_i
 #pragma unroll (n <= 8 ? 32 : 1)
-      for (int a = 0; a < n; ++a)
+      for (int a = 0; a < n; ++a) {
+        R s = zero, t = zero;
 #pragma unroll (n <= 8 ? 32 : 1)
-        for (int c = 0; c < n; ++c) Kmu[a] = fma(Kon[c * n + a], mnext[c], Kmu[a]);
+        for (int c = 0; c < n; ++c) {
+          s = r_fma(E[c * n + a], mnext[c], s);
+          t = r_fma(E[a * n + c], mi[c], t);
+        }
+        Kmu[a] = Kmu[a] + s;
+        q[a] = t;
+      }
+      R B[nn];
+      ld_blk<n, R>(Lo + (size_t)i * nn, B);
+#pragma unroll (n <= 8 ? 32 : 1)
+      for (int e = 0; e < nn; ++e) E[e] = r_fma(beta, E[e], B[e]);   // beta K^-1_{i+1,i} + Lambda_{i+1,i}
     }
-    double y[n], z[n];
+    R y[n], z[n];
 #pragma unroll (n <= 8 ? 32 : 1)
     for (int a = 0; a < n; ++a) {
-      double r = beta * (-P.g[(size_t)i * n + a] + P.b[(size_t)i * n + a] - Kmu[a]);
-#pragma unroll (n <= 8 ? 32 : 1)
-      for (int c = 0; c < n; ++c) r = fma(-WMp[a * n + c], yp[c], r);
-      y[a] = r;
+      R r = (bb[(size_t)i * n + a] - gg[(size_t)i * n + a]) - Kmu[a];
+      y[a] = r_fma(beta, r, -vM[a]);
     }
 #pragma unroll (n <= 8 ? 32 : 1)
     for (int a = 0; a < n; ++a) {
-      double s = 0.0;
+      R s = CiM[pk(a, 0)] * y[0];
 #pragma unroll (n <= 8 ? 32 : 1)
-      for (int c = 0; c < n; ++c) s = fma(CiM[a * n + c], y[c], s);
+      for (int c = 1; c < n; ++c) s = r_fma(CiM[pk(a, c)], y[c], s);
       z[a] = s;
     }
-    double* sp = P.scr + (size_t)i * SS;
-    st_blk<n>(sp, CiA);
-    st_vec<n>(sp + 3 * nn, z);
+    R* sp = scr + (size_t)i * SS;
+    st_packed<n, R>(sp + Scr<n>::oCi, CiA);
+    st_vec<n, R>(sp + Scr<n>::oZ, z);
     if (i < N) {
-      double WA[nn];
+      R W[nn];
+      mul_full_sym<n, R>(E, CiA, W);
+      mul_nt_packed<n, R>(W, E, SA);
+      st_blk<n, R>(sp + Scr<n>::oWA, W);
+      mul_full_sym<n, R>(E, CiM, W);
+      mul_nt_packed<n, R>(W, E, SM);
 #pragma unroll (n <= 8 ? 32 : 1)
-      for (int e = 0; e < nn; ++e) En[e] = fma(beta, Kon[e], En[e]);
-      mul_nn<n>(En, CiA, WA);
-      mul_nn<n>(En, CiM, WMp);
-      mul_nt_sym<n>(WA, En, SA);
-      mul_nt_sym<n>(WMp, En, SM);
-      st_blk<n>(sp + nn, WA);
-      st_blk<n>(sp + 2 * nn, WMp);
-    }
+      for (int a = 0; a < n; ++a) {
+        R s = W[a * n] * y[0];
 #pragma unroll (n <= 8 ? 32 : 1)
-    for (int a = 0; a < n; ++a) {
-      yp[a] = y[a];
-      mprev[a] = mi[a];
-      mi[a] = mnext[a];
+        for (int c = 1; c < n; ++c) s = r_fma(W[a * n + c], y[c], s);
+        vM[a] = s;
+      }
+      st_blk<n, R>(sp + Scr<n>::oWM, W);
+#pragma unroll (n <= 8 ? 32 : 1)
+      for (int a = 0; a < n; ++a) mi[a] = mnext[a];
     }
   }
-  if (!okA || !okM) return R;
-  R.pd = true;
-  const double D = (double)n * (N + 1);
-  const double bp1 = beta + 1.0;
-  R.logdet = ldA.log_value() - D * log(bp1);
+  if (!okA || !okM) return res;
+  res.pd = true;
+  const double Dd = (double)n * (N + 1);
+  const double bp1d = beta_d + 1.0;
+  res.logdet = ldA.log_value() - Dd * log(bp1d);
+  const R bp1 = r_from<R>(bp1d), mbp1 = -bp1;
   // backward sweep
-  double Sn[nn], xn[n];
-  double trc = 0.0, dl = 0.0, ktr = 0.0, kq = 0.0, dpn[n];
+  R* mo_out = rp<R>(P.mu[out]);
+  R* Sd_out = rp<R>(P.Sd[out]);
+  R* So_out = rp<R>(P.So[out]);
+  R Sn[np], xn[n], dpn[n];
+  R trc = zero, dl = zero, ktr = zero, kq = zero;
   {
-    const double* sp = P.scr + (size_t)N * SS;
-    ld_blk<n>(sp, Sn);
-    ld_vec<n>(sp + 3 * nn, xn);
-    double Kd[nn], Lb[nn], Gb[nn];
-    ld_blk<n>(P.Kd + (size_t)N * nn, Kd);
-    ld_blk<n>(P.Ld + (size_t)N * nn, Lb);
-    ld_blk<n>(P.G + (size_t)N * nn, Gb);
-    for (int e = 0; e < nn; ++e) {
-      trc = fma(Lb[e] - 2.0 * Gb[e] - Kd[e], Sn[e], trc);
-      ktr = fma(Kd[e], Sn[e], ktr);
-    }
-    double mo[n];
+    const R* sp = scr + (size_t)N * SS;
+    ld_packed<n, R>(sp + Scr<n>::oCi, Sn);
+    ld_vec<n, R>(sp + Scr<n>::oZ, xn);
+    R B[nn], Lb[nn];
+    ld_blk<n, R>(Ld + (size_t)N * nn, Lb);
+    ld_blk<n, R>(GG + (size_t)N * nn, B);
+    for (int a = 0; a < n; ++a)
+      for (int c = 0; c < n; ++c) trc = r_fma(Lb[a * n + c] - (B[a * n + c] + B[a * n + c]), Sn[pk(a, c)], trc);
+    for (int a = 0; a < n; ++a)
+      for (int c = 0; c < n; ++c) dl = r_fma(xn[a] * Lb[a * n + c], xn[c], dl);
+    ld_blk<n, R>(Kd + (size_t)N * nn, B);
+    R mo[n];
     for (int a = 0; a < n; ++a) {
       mo[a] = mu[(size_t)N * n + a] + xn[a];
-      dpn[a] = mo[a] - P.mubar[(size_t)N * n + a];
+      dpn[a] = mo[a] - mubar[(size_t)N * n + a];
     }
     for (int a = 0; a < n; ++a)
       for (int c = 0; c < n; ++c) {
-        dl = fma(xn[a] * Lb[a * n + c], xn[c], dl);
-        kq = fma(dpn[a] * Kd[a * n + c], dpn[c], kq);
+        trc = r_fma(-B[a * n + c], Sn[pk(a, c)], trc);
+        ktr = r_fma(B[a * n + c], Sn[pk(a, c)], ktr);
+        kq = r_fma(dpn[a] * B[a * n + c], dpn[c], kq);
       }
-    st_blk_scaled<n>(P.Sd[out] + (size_t)N * nn, Sn, bp1);
-    st_vec<n>(P.mu[out] + (size_t)N * n, mo);
+    R Sfull[np];
+    for (int e = 0; e < np; ++e) Sfull[e] = bp1 * Sn[e];
+    st_sym<n, R>(Sd_out + (size_t)N * nn, Sfull);
+    st_vec<n, R>(mo_out + (size_t)N * n, mo);
   }
   for (int i = N - 1; i >= 0; --i) {
-    const double* sp = P.scr + (size_t)i * SS;
-    double CiA[nn], WA[nn], WM[nn], z[n], T[nn], Si[nn], xi[n];
-    ld_blk<n>(sp, CiA);
-    ld_blk<n>(sp + nn, WA);
-    ld_blk<n>(sp + 2 * nn, WM);
-    ld_vec<n>(sp + 3 * nn, z);
-    mul_nn<n>(Sn, WA, T);
-    add_tn_sym<n>(CiA, WA, T, Si);
-#pragma unroll (n <= 8 ? 32 : 1)
-    for (int a = 0; a < n; ++a) {
-      double s = z[a];
-#pragma unroll (n <= 8 ? 32 : 1)
-      for (int c = 0; c < n; ++c) s = fma(-WM[c * n + a], xn[c], s);
-      xi[a] = s;
+    const R* sp = scr + (size_t)i * SS;
+    R Si[np], T[nn], xi[n];
+    {
+      R W[nn], Ci[np];
+      ld_blk<n, R>(sp + Scr<n>::oWA, W);
+      ld_packed<n, R>(sp + Scr<n>::oCi, Ci);
+      mul_sym_full<n, R>(Sn, W, T);            // T = Sigma~_{i+1} W_i = -Sigma~_{i+1,i}
+      add_tn_packed<n, R>(Ci, W, T, Si);
     }
-    double Kd[nn], Lb[nn], Gb[nn], Ko[nn], Lo[nn];
-    ld_blk<n>(P.Kd + (size_t)i * nn, Kd);
-    ld_blk<n>(P.Ld + (size_t)i * nn, Lb);
-    ld_blk<n>(P.G + (size_t)i * nn, Gb);
-    ld_blk<n>(P.Ko + (size_t)i * nn, Ko);
-    ld_blk<n>(P.Lo + (size_t)i * nn, Lo);
+    {
+      R WM[nn], z[n];
+      ld_blk<n, R>(sp + Scr<n>::oWM, WM);
+      ld_vec<n, R>(sp + Scr<n>::oZ, z);
 #pragma unroll (n <= 8 ? 32 : 1)
-    for (int e = 0; e < nn; ++e) {
-      // Sigma~_{i+1,i} = -T
-      trc = fma(Lb[e] - 2.0 * Gb[e] - Kd[e], Si[e], trc);
-      trc = fma(-2.0 * (Lo[e] - Ko[e]), T[e], trc);
-      ktr = fma(Kd[e], Si[e], fma(-2.0 * Ko[e], T[e], ktr));
+      for (int a = 0; a < n; ++a) {
+        R s = z[a];
+#pragma unroll (n <= 8 ? 32 : 1)
+        for (int c = 0; c < n; ++c) s = r_fma(-WM[c * n + a], xn[c], s);
+        xi[a] = s;
+      }
     }
-    double mo[n], dpi[n];
+    R mo[n], dpi[n];
 #pragma unroll (n <= 8 ? 32 : 1)
     for (int a = 0; a < n; ++a) {
       mo[a] = mu[(size_t)i * n + a] + xi[a];
-      dpi[a] = mo[a] - P.mubar[(size_t)i * n + a];
+      dpi[a] = mo[a] - mubar[(size_t)i * n + a];
+    }
+    {
+      R B[nn];
+      ld_blk<n, R>(Ld + (size_t)i * nn, B);    // Lambda_k: trace, delta^T Lambda_k delta
+#pragma unroll (n <= 8 ? 32 : 1)
+      for (int a = 0; a < n; ++a)
+#pragma unroll (n <= 8 ? 32 : 1)
+        for (int c = 0; c < n; ++c) {
+          trc = r_fma(B[a * n + c], Si[pk(a, c)], trc);
+          dl = r_fma(xi[a] * B[a * n + c], xi[c], dl);
+        }
+      ld_blk<n, R>(GG + (size_t)i * nn, B);
+#pragma unroll (n <= 8 ? 32 : 1)
+      for (int a = 0; a < n; ++a)
+#pragma unroll (n <= 8 ? 32 : 1)
+        for (int c = 0; c < n; ++c) trc = r_fma(-(B[a * n + c] + B[a * n + c]), Si[pk(a, c)], trc);
+      ld_blk<n, R>(Kd + (size_t)i * nn, B);
+#pragma unroll (n <= 8 ? 32 : 1)
+      for (int a = 0; a < n; ++a)
+#pragma unroll (n <= 8 ? 32 : 1)
+        for (int c = 0; c < n; ++c) {
+          trc = r_fma(-B[a * n + c], Si[pk(a, c)], trc);
+          ktr = r_fma(B[a * n + c], Si[pk(a, c)], ktr);
+          kq = r_fma(dpi[a] * B[a * n + c], dpi[c], kq);
+        }
+      ld_blk<n, R>(Lo + (size_t)i * nn, B);
+#pragma unroll (n <= 8 ? 32 : 1)
+      for (int a = 0; a < n; ++a)
+#pragma unroll (n <= 8 ? 32 : 1)
+        for (int c = 0; c < n; ++c) {
+          trc = r_fma(-(B[a * n + c] + B[a * n + c]), T[a * n + c], trc);
+          dl = r_fma((xn[a] + xn[a]) * B[a * n + c], xi[c], dl);
+        }
+      ld_blk<n, R>(Ko + (size_t)i * nn, B);
+#pragma unroll (n <= 8 ? 32 : 1)
+      for (int a = 0; a < n; ++a)
+#pragma unroll (n <= 8 ? 32 : 1)
+        for (int c = 0; c < n; ++c) {
+          trc = r_fma(B[a * n + c] + B[a * n + c], T[a * n + c], trc);
+          ktr = r_fma(-(B[a * n + c] + B[a * n + c]), T[a * n + c], ktr);
+          kq = r_fma((dpn[a] + dpn[a]) * B[a * n + c], dpi[c], kq);
+        }
+    }
+    {
+      R X[np];
+#pragma unroll (n <= 8 ? 32 : 1)
+      for (int e = 0; e < np; ++e) X[e] = bp1 * Si[e];
+      st_sym<n, R>(Sd_out + (size_t)i * nn, X);
+#pragma unroll (n <= 8 ? 32 : 1)
+      for (int e = 0; e < nn; ++e) T[e] = mbp1 * T[e];
+      st_blk<n, R>(So_out + (size_t)i * nn, T);
+      st_vec<n, R>(mo_out + (size_t)i * n, mo);
     }
 #pragma unroll (n <= 8 ? 32 : 1)
-    for (int a = 0; a < n; ++a)
-#pragma unroll (n <= 8 ? 32 : 1)
-      for (int c = 0; c < n; ++c) {
-        dl = fma(xi[a] * Lb[a * n + c], xi[c], dl);
-        dl = fma(2.0 * xn[a] * Lo[a * n + c], xi[c], dl);
-        kq = fma(dpi[a] * Kd[a * n + c], dpi[c], kq);
-        kq = fma(2.0 * dpn[a] * Ko[a * n + c], dpi[c], kq);
-      }
-    st_blk_scaled<n>(P.Sd[out] + (size_t)i * nn, Si, bp1);
-    st_blk_scaled<n>(P.So[out] + (size_t)i * nn, T, -bp1);
-    st_vec<n>(P.mu[out] + (size_t)i * n, mo);
-#pragma unroll (n <= 8 ? 32 : 1)
-    for (int e = 0; e < nn; ++e) Sn[e] = Si[e];
+    for (int e = 0; e < np; ++e) Sn[e] = Si[e];
 #pragma unroll (n <= 8 ? 32 : 1)
     for (int a = 0; a < n; ++a) {
       xn[a] = xi[a];
       dpn[a] = dpi[a];
     }
   }
-  R.trace = beta * trc;
-  R.delta = dl;
-  R.kl = 0.5 * (R.trace + dl + R.logdet - logdet_k);
-  R.prior_cost = 0.5 * (bp1 * ktr + kq);
-  return R;
+  res.trace = beta_d * r_to(trc);
+  res.delta = r_to(dl);
+  res.kl = 0.5 * (res.trace + res.delta + res.logdet - logdet_k);
+  res.prior_cost = 0.5 * (bp1d * r_to(ktr) + r_to(kq));
+  return res;
 }
 
 // Lambda_{k+1} = A~(beta) / (beta+1), written over (Ld, Lo).
-template <int n>
-PGV_BIG void accept_precision(const PlanDesc& P, double beta) {
+template <int n, typename R>
+PGV_BIG void accept_precision(const PlanDesc& P, double beta_d) {
   constexpr int nn = n * n;
   const int N = P.N;
-  const double inv = 1.0 / (beta + 1.0);
+  const R inv = r_from<R>(1.0 / (beta_d + 1.0)), beta = r_from<R>(beta_d), two = r_fromf<R>(2.0f);
+  R* Ld = rp<R>(P.Ld);
+  R* Lo = rp<R>(P.Lo);
+  const R* Kd = rp<R>(P.Kd);
+  const R* Ko = rp<R>(P.Ko);
+  const R* GG = rp<R>(P.G);
   for (int i = 0; i <= N; ++i) {
-    double Kd[nn], Lb[nn], Gb[nn];
-    ld_blk<n>(P.Kd + (size_t)i * nn, Kd);
-    ld_blk<n>(P.Ld + (size_t)i * nn, Lb);
-    ld_blk<n>(P.G + (size_t)i * nn, Gb);
-    for (int e = 0; e < nn; ++e) Lb[e] = (fma(beta, fma(2.0, Gb[e], Kd[e]), Lb[e])) * inv;
-    st_blk<n>(P.Ld + (size_t)i * nn, Lb);
+    R K[nn], Lb[nn], Gb[nn];
+    ld_blk<n, R>(Kd + (size_t)i * nn, K);
+    ld_blk<n, R>(Ld + (size_t)i * nn, Lb);
+    ld_blk<n, R>(GG + (size_t)i * nn, Gb);
+#pragma unroll (n <= 8 ? 32 : 1)
+    for (int e = 0; e < nn; ++e) Lb[e] = r_fma(beta, r_fma(two, Gb[e], K[e]), Lb[e]) * inv;
+    st_blk<n, R>(Ld + (size_t)i * nn, Lb);
     if (i < N) {
-      double Ko[nn], Lo[nn];
-      ld_blk<n>(P.Ko + (size_t)i * nn, Ko);
-      ld_blk<n>(P.Lo + (size_t)i * nn, Lo);
-      for (int e = 0; e < nn; ++e) Lo[e] = fma(beta, Ko[e], Lo[e]) * inv;
-      st_blk<n>(P.Lo + (size_t)i * nn, Lo);
+      ld_blk<n, R>(Ko + (size_t)i * nn, K);
+      ld_blk<n, R>(Lo + (size_t)i * nn, Lb);
+#pragma unroll (n <= 8 ? 32 : 1)
+      for (int e = 0; e < nn; ++e) Lb[e] = r_fma(beta, K[e], Lb[e]) * inv;
+      st_blk<n, R>(Lo + (size_t)i * nn, Lb);
     }
   }
 }
 
-// One proximal iteration (Alg. 1 loop body) for the plan: quadrature and
-// gradients at the current iterate, the largest feasible step by bisection
-// (App. C: beta_max first, then max_bisect halvings of [0, beta_max]; feasible
-// = Lambda' positive definite and KL <= eps), and the update.
-template <int n, typename QT>
+// One proximal iteration (Alg. 1 loop body): quadrature and gradients at the
+// current iterate, the largest feasible step by bisection (App. C: beta_max
+// first, then max_bisect halvings of [0, beta_max]; feasible = Lambda'
+// positive definite and KL <= eps, decided in FP64), and the update.
+template <int n, typename QT, typename R>
 PGV_BIG void iterate_once(const PlanDesc& P) {
   double* sc = P.scal;
   const int cur = (int)sc[S_CUR];
   const int oa = (cur + 1) % 3, ob = (cur + 2) % 3;
   double coll;
-  if (!quad_all<n, QT>(P, cur, coll)) {
+  if (!quad_all<n, QT, R>(P, cur, coll)) {
     sc[S_STATUS] = 3.0;
     return;
   }
@@ -731,19 +901,18 @@ PGV_BIG void iterate_once(const PlanDesc& P) {
   bestR.kl = 0.0;
   bestR.logdet = logdet_k;
   bestR.prior_cost = sc[S_PRIOR];
-  // beta_max first; if infeasible, max_bisect halvings of [0, beta_max]
   double beta = P.beta_max, lo = 0.0, hi = P.beta_max;
   int into = oa, halvings = 0;
   bool searching = false;
   for (;;) {
-    TrialOut R = trial<n>(P, beta, cur, into, logdet_k);
+    TrialOut Rt = trial<n, R>(P, beta, cur, into, logdet_k);
     ++trials;
-    if (R.pd && has_eps) margin = fmin(margin, fabs(R.kl - eps) / eps);
-    const bool feas = R.pd && (R.kl <= eps);
+    if (Rt.pd && has_eps) margin = fmin(margin, fabs(Rt.kl - eps) / eps);
+    const bool feas = Rt.pd && (Rt.kl <= eps);
     if (feas) {
       best = into;
       best_beta = beta;
-      bestR = R;
+      bestR = Rt;
     }
     if (!searching) {
       if (feas) break;
@@ -771,7 +940,7 @@ PGV_BIG void iterate_once(const PlanDesc& P) {
     P.log[k] = li;
   }
   if (best >= 0) {
-    accept_precision<n>(P, best_beta);
+    accept_precision<n, R>(P, best_beta);
     sc[S_CUR] = (double)best;
     sc[S_LOGDET] = bestR.logdet;
     sc[S_PRIOR] = bestR.prior_cost;
@@ -781,40 +950,44 @@ PGV_BIG void iterate_once(const PlanDesc& P) {
   sc[S_KIN] = sc[S_KIN] + 1.0;
 }
 
-// Initial iterate (mu_0 straight line in q with constant qdot; Lambda_0 = K^-1
-// or init_scale * I) and its marginals.
-template <int n>
+// Initial iterate (mu_0 on the straight line in q with constant qdot;
+// Lambda_0 = K^-1 or init_scale * I) and its marginals.
+template <int n, typename R>
 PGV_BIG void init_plan(const PlanDesc& P) {
   constexpr int nn = n * n;
   double* sc = P.scal;
   const int N = P.N, nq = P.nq;
+  R* mu0 = rp<R>(P.mu[0]);
   for (int i = 0; i <= N; ++i) {
     double s = (double)i / N;
     for (int a = 0; a < nq; ++a) {
       double d = P.muN[a] - P.mu0[a];
-      P.mu[0][(size_t)i * n + a] = P.mu0[a] + s * d;
-      P.mu[0][(size_t)i * n + nq + a] = d / P.T;
+      mu0[(size_t)i * n + a] = r_from<R>(P.mu0[a] + s * d);
+      mu0[(size_t)i * n + nq + a] = r_from<R>(d / P.T);
     }
   }
+  R* Ld = rp<R>(P.Ld);
+  R* Lo = rp<R>(P.Lo);
+  const R zero = r_fromf<R>(0.0f), sI = r_from<R>(P.init_scale);
   for (int i = 0; i <= N; ++i) {
-    double blk[nn];
+    R blk[nn];
     if (P.init_kind == 1) {
-      for (int e = 0; e < nn; ++e) blk[e] = 0.0;
-      for (int a = 0; a < n; ++a) blk[a * n + a] = P.init_scale;
+      for (int e = 0; e < nn; ++e) blk[e] = zero;
+      for (int a = 0; a < n; ++a) blk[a * n + a] = sI;
     } else {
-      ld_blk<n>(P.Kd + (size_t)i * nn, blk);
+      ld_blk<n, R>(rp<R>(P.Kd) + (size_t)i * nn, blk);
     }
-    st_blk<n>(P.Ld + (size_t)i * nn, blk);
+    st_blk<n, R>(Ld + (size_t)i * nn, blk);
     if (i < N) {
       if (P.init_kind == 1)
-        for (int e = 0; e < nn; ++e) blk[e] = 0.0;
+        for (int e = 0; e < nn; ++e) blk[e] = zero;
       else
-        ld_blk<n>(P.Ko + (size_t)i * nn, blk);
-      st_blk<n>(P.Lo + (size_t)i * nn, blk);
+        ld_blk<n, R>(rp<R>(P.Ko) + (size_t)i * nn, blk);
+      st_blk<n, R>(Lo + (size_t)i * nn, blk);
     }
   }
   double ld, pc;
-  if (!marginals<n>(P, P.Ld, P.Lo, 0, ld, pc)) {
+  if (!marginals<n, R>(P, 0, ld, pc)) {
     sc[S_STATUS] = 2.0;
     return;
   }
@@ -824,6 +997,7 @@ PGV_BIG void init_plan(const PlanDesc& P) {
   sc[S_K] = 0.0;
   sc[S_KIN] = 0.0;
   sc[S_INIT] = 1.0;
+  sc[S_FMT] = 0.0;
 }
 
 // ------------------------------------------------------------ SLR (a6)
@@ -915,13 +1089,16 @@ PGV_DEV bool slr_step(const PlanDesc& P, const double* xbar, const double* Sbar,
   return true;
 }
 
-template <int n, typename QT>
+template <int n, typename QT, typename R>
 PGV_BIG bool slr_all(const PlanDesc& P, bool first) {
   constexpr int nn = n * n;
   const int N = P.N, nq = P.nq;
   double xb[n], Sb[nn];
   bool ok = true;
-  for (int i = 0; i < N; ++i) {
+  const int cur = (int)P.scal[S_CUR];
+  const R* mu = rp<R>(P.mu[cur]);
+  const R* Sd = rp<R>(P.Sd[cur]);
+  for (int i = 0; i <= N; ++i) {
     if (first) {
       double s = (double)i / N;
       for (int a = 0; a < nq; ++a) {
@@ -931,25 +1108,11 @@ PGV_BIG bool slr_all(const PlanDesc& P, bool first) {
       }
       for (int e = 0; e < nn; ++e) Sb[e] = P.K0[e];
     } else {
-      const int cur = (int)P.scal[S_CUR];
-      ld_vec<n>(P.mu[cur] + (size_t)i * n, xb);
-      ld_blk<n>(P.Sd[cur] + (size_t)i * nn, Sb);
+      for (int a = 0; a < n; ++a) xb[a] = r_to(mu[(size_t)i * n + a]);
+      for (int e = 0; e < nn; ++e) Sb[e] = r_to(Sd[(size_t)i * nn + e]);
     }
-    st_vec<n>(P.xbar + (size_t)i * n, xb);
-    ok = slr_step<n, QT>(P, xb, Sb, P.Altv + (size_t)i * nn, P.altv + (size_t)i * n) && ok;
-  }
-  if (first) {
-    double s = 1.0;
-    for (int a = 0; a < nq; ++a) {
-      double d = P.muN[a] - P.mu0[a];
-      xb[a] = P.mu0[a] + s * d;
-      xb[nq + a] = d / P.T;
-    }
-    st_vec<n>(P.xbar + (size_t)N * n, xb);
-  } else {
-    const int cur = (int)P.scal[S_CUR];
-    ld_vec<n>(P.mu[cur] + (size_t)N * n, xb);
-    st_vec<n>(P.xbar + (size_t)N * n, xb);
+    for (int a = 0; a < n; ++a) P.xbar[(size_t)i * n + a] = xb[a];
+    if (i < N) ok = slr_step<n, QT>(P, xb, Sb, P.Altv + (size_t)i * nn, P.altv + (size_t)i * n) && ok;
   }
   return ok;
 }
@@ -962,99 +1125,136 @@ PGV_BIG bool slr_all(const PlanDesc& P, bool first) {
   const PlanDesc& P = descs[t];
 
 // Prior build; `mode` 0: linear system (A, a); 1: the SLR linearisation.
-template <int n>
+template <int n, typename R>
 __global__ void k_prior(const PlanDesc* __restrict__ descs, int count, int mode) {
   PLAN_OR_RETURN
   if (P.scal[S_STATUS] != 0.0) return;
-  if (!prior_build<n>(P, mode == 1)) P.scal[S_STATUS] = 1.0;
+  if (!prior_build<n, R>(P, mode == 1)) P.scal[S_STATUS] = 1.0;
 }
 
-template <int n>
+template <int n, typename R>
 __global__ void k_init(const PlanDesc* __restrict__ descs, int count) {
   PLAN_OR_RETURN
   if (P.scal[S_STATUS] != 0.0) return;
-  init_plan<n>(P);
+  init_plan<n, R>(P);
 }
 
 // After a relinearisation: the prior cost of the current iterate under the
 // new prior, and a fresh inner-iteration counter.
-template <int n>
+template <int n, typename R>
 __global__ void k_relinearised(const PlanDesc* __restrict__ descs, int count) {
   PLAN_OR_RETURN
   if (P.scal[S_STATUS] != 0.0) return;
-  P.scal[S_PRIOR] = prior_cost_of<n>(P, (int)P.scal[S_CUR]);
+  P.scal[S_PRIOR] = prior_cost_of<n, R>(P, (int)P.scal[S_CUR]);
   P.scal[S_KIN] = 0.0;
 }
 
-template <int n, typename QT>
+template <int n, typename QT, typename R>
 __global__ void __launch_bounds__(64) k_iterate(const PlanDesc* __restrict__ descs, int count, int iters) {
   PLAN_OR_RETURN
   for (int it = 0; it < iters; ++it) {
     if (P.scal[S_STATUS] != 0.0 || P.scal[S_INIT] == 0.0) return;
     if ((int)P.scal[S_KIN] >= P.iters) return;
-    iterate_once<n, QT>(P);
+    iterate_once<n, QT, R>(P);
   }
 }
 
-// SLR linearisation.  mode 1: the straight-line nominal with K0 (first
-// outer iteration); 0: the current iterate, closing the previous outer
-// iteration (its norm); 2: the current iterate without bookkeeping.
-template <int n, typename QT>
+template <int n, typename R>
+PGV_DEV double slr_norm(const PlanDesc& P) {
+  const int cur = (int)P.scal[S_CUR];
+  const R* mu = rp<R>(P.mu[cur]);
+  double s = 0.0;
+  for (size_t e = 0; e < (size_t)(P.N + 1) * n; ++e) {
+    double d = r_to(mu[e]) - P.xbar[e];
+    s = fma(d, d, s);
+  }
+  return sqrt(s);
+}
+
+// SLR linearisation.  mode 1: the straight-line nominal with K0 (first outer
+// iteration); 0: the current iterate, closing the previous outer iteration
+// (its norm); 2: the current iterate without bookkeeping.
+template <int n, typename QT, typename R>
 __global__ void k_slr(const PlanDesc* __restrict__ descs, int count, int mode) {
   PLAN_OR_RETURN
   if (P.scal[S_STATUS] != 0.0) return;
-  const int first = (mode == 1);
   if (mode == 0) {
-    // ||xbar^{j+1} - xbar^j||: the finished linearisation's result vs its nominal
-    const int cur = (int)P.scal[S_CUR];
     const int j = (int)P.scal[S_J];
-    double s = 0.0;
-    for (size_t e = 0; e < (size_t)(P.N + 1) * n; ++e) {
-      double d = P.mu[cur][e] - P.xbar[e];
-      s = fma(d, d, s);
-    }
-    if (j < P.slr_iters) P.slr_norms[j] = sqrt(s);
+    if (j < P.slr_iters) P.slr_norms[j] = slr_norm<n, R>(P);
     P.scal[S_J] = (double)(j + 1);
   }
-  if (!slr_all<n, QT>(P, first != 0)) P.scal[S_STATUS] = 4.0;
+  if (!slr_all<n, QT, R>(P, mode == 1)) P.scal[S_STATUS] = 4.0;
 }
 
 // Final SLR norm after the last linearisation's iterations.
-template <int n>
+template <int n, typename R>
 __global__ void k_slr_finish(const PlanDesc* __restrict__ descs, int count) {
   PLAN_OR_RETURN
   if (P.scal[S_STATUS] != 0.0) return;
-  const int cur = (int)P.scal[S_CUR];
   const int j = (int)P.scal[S_J];
-  double s = 0.0;
-  for (size_t e = 0; e < (size_t)(P.N + 1) * n; ++e) {
-    double d = P.mu[cur][e] - P.xbar[e];
-    s = fma(d, d, s);
-  }
-  if (j < P.slr_iters) P.slr_norms[j] = sqrt(s);
+  if (j < P.slr_iters) P.slr_norms[j] = slr_norm<n, R>(P);
   P.scal[S_J] = (double)(j + 1);
 }
 
-// Moves the current iterate into buffer set 0 (the one results are read from).
-template <int n>
+// Moves the current iterate into buffer set 0 (the one results are read
+// from); with double-float storage also converts the result buffers (set 0,
+// Lambda) to FP64 in place.  k_working undoes that conversion.
+template <int n, typename R>
 __global__ void k_finalize(const PlanDesc* __restrict__ descs, int count) {
   PLAN_OR_RETURN
   const int cur = (int)P.scal[S_CUR];
-  if (cur == 0) return;
   const size_t N = P.N;
-  for (size_t e = 0; e < (N + 1) * n; ++e) P.mu[0][e] = P.mu[cur][e];
-  for (size_t e = 0; e < (N + 1) * n * n; ++e) P.Sd[0][e] = P.Sd[cur][e];
-  for (size_t e = 0; e < N * n * n; ++e) P.So[0][e] = P.So[cur][e];
-  P.scal[S_CUR] = 0.0;
+  if (cur != 0 && P.scal[S_FMT] == 0.0) {
+    R* m0 = rp<R>(P.mu[0]);
+    R* s0 = rp<R>(P.Sd[0]);
+    R* o0 = rp<R>(P.So[0]);
+    const R* mc = rp<R>(P.mu[cur]);
+    const R* sc = rp<R>(P.Sd[cur]);
+    const R* oc = rp<R>(P.So[cur]);
+    for (size_t e = 0; e < (N + 1) * n; ++e) m0[e] = mc[e];
+    for (size_t e = 0; e < (N + 1) * n * n; ++e) s0[e] = sc[e];
+    for (size_t e = 0; e < N * n * n; ++e) o0[e] = oc[e];
+    P.scal[S_CUR] = 0.0;
+  }
+  if (!std::is_same<R, double>::value && P.scal[S_FMT] == 0.0) {
+    double* bufs[5] = {P.mu[0], P.Sd[0], P.So[0], P.Ld, P.Lo};
+    const size_t cnt[5] = {(N + 1) * n, (N + 1) * n * n, N * n * n, (N + 1) * n * n, N * n * n};
+    for (int k = 0; k < 5; ++k) {
+      R* rbuf = rp<R>(bufs[k]);
+      for (size_t e = 0; e < cnt[k]; ++e) {
+        double v = r_to(rbuf[e]);
+        bufs[k][e] = v;
+      }
+    }
+    P.scal[S_FMT] = 1.0;
+  }
 }
 
-// Single-row phases (for per-row checks through the C ABI).
+template <int n, typename R>
+__global__ void k_working(const PlanDesc* __restrict__ descs, int count) {
+  PLAN_OR_RETURN
+  const size_t N = P.N;
+  if (!std::is_same<R, double>::value && P.scal[S_FMT] == 1.0) {
+    double* bufs[5] = {P.mu[0], P.Sd[0], P.So[0], P.Ld, P.Lo};
+    const size_t cnt[5] = {(N + 1) * n, (N + 1) * n * n, N * n * n, (N + 1) * n * n, N * n * n};
+    for (int k = 0; k < 5; ++k) {
+      R* rbuf = rp<R>(bufs[k]);
+      for (size_t e = 0; e < cnt[k]; ++e) {
+        R v = r_from<R>(bufs[k][e]);
+        rbuf[e] = v;
+      }
+    }
+    P.scal[S_FMT] = 0.0;
+  }
+}
+
+// Single-row phases (per-row checks through the C ABI), FP64 recursions.
 template <int n>
 __global__ void k_marginals(const PlanDesc* __restrict__ descs, int count) {
   PLAN_OR_RETURN
   double ld, pc;
   const int cur = (int)P.scal[S_CUR];
-  bool ok = marginals<n>(P, P.Ld, P.Lo, cur, ld, pc);
+  bool ok = marginals<n, double>(P, cur, ld, pc);
   P.scal[S_LOGDET] = ld;
   P.scal[S_PRIOR] = pc;
   if (!ok) P.scal[S_STATUS] = 2.0;
@@ -1064,7 +1264,7 @@ template <int n, typename QT>
 __global__ void k_quad(const PlanDesc* __restrict__ descs, int count) {
   PLAN_OR_RETURN
   double coll;
-  bool ok = quad_all<n, QT>(P, (int)P.scal[S_CUR], coll);
+  bool ok = quad_all<n, QT, double>(P, (int)P.scal[S_CUR], coll);
   P.scal[S_COLL] = coll;
   if (!ok) P.scal[S_STATUS] = 3.0;
 }
@@ -1073,7 +1273,7 @@ template <int n>
 __global__ void k_trial(const PlanDesc* __restrict__ descs, int count, double beta) {
   PLAN_OR_RETURN
   const int cur = (int)P.scal[S_CUR];
-  TrialOut R = trial<n>(P, beta, cur, (cur + 2) % 3, P.scal[S_LOGDET]);
+  TrialOut R = trial<n, double>(P, beta, cur, (cur + 2) % 3, P.scal[S_LOGDET]);
   P.scal[S_T_LOGDET] = R.logdet;
   P.scal[S_T_KL] = R.kl;
   P.scal[S_T_PD] = R.pd ? 1.0 : 0.0;
@@ -1088,33 +1288,35 @@ static inline int blocks_for(int count, int tpb) { return (count + tpb - 1) / tp
 
 // Launch groups; each is instantiated in its own translation unit so that the
 // (fully inlined) kernels of one state dimension compile in parallel.
-//   iter<n, QT>: the fused proximal iterations (Alg. 1 loop);
-//   aux<n>:      prior build, initial iterate, SLR, bookkeeping kernels;
-//   rows<n>:     the single-row kernels (marginals, quadrature, one trial).
+//   iter<n, QT, R>: the fused proximal iterations (Alg. 1 loop);
+//   aux<n, R>:      prior build, initial iterate, SLR, bookkeeping kernels;
+//   rows<n>:        the single-row kernels (marginals, quadrature, one trial).
 enum { PH_PRIOR = 100, PH_INIT = 101, PH_ITER = 102, PH_SLR = 103, PH_RELIN = 104, PH_SLR_FIN = 105,
-       PH_FINALIZE = 106 };
+       PH_FINALIZE = 106, PH_WORKING = 107 };
 
-template <int n, typename QT>
+template <int n, typename QT, typename R>
 cudaError_t launch_iter(const Launch& L, int iters) {
   const int tpb = 32;
-  k_iterate<n, QT><<<blocks_for(L.count, tpb), tpb, 0, L.stream>>>(L.descs, L.count, iters);
+  k_iterate<n, QT, R><<<blocks_for(L.count, tpb), tpb, 0, L.stream>>>(L.descs, L.count, iters);
   return cudaGetLastError();
 }
 
-template <int n>
-cudaError_t launch_aux(const Launch& L, int phase, int arg_i, int mixed) {
+// `qt32`: FP32 quadrature in the SLR kernel.
+template <int n, typename R>
+cudaError_t launch_aux(const Launch& L, int phase, int arg_i, int qt32) {
   const int tpb = 32;
   dim3 g(blocks_for(L.count, tpb)), b(tpb);
   switch (phase) {
-    case PH_PRIOR: k_prior<n><<<g, b, 0, L.stream>>>(L.descs, L.count, arg_i); break;
-    case PH_INIT: k_init<n><<<g, b, 0, L.stream>>>(L.descs, L.count); break;
+    case PH_PRIOR: k_prior<n, R><<<g, b, 0, L.stream>>>(L.descs, L.count, arg_i); break;
+    case PH_INIT: k_init<n, R><<<g, b, 0, L.stream>>>(L.descs, L.count); break;
     case PH_SLR:
-      if (mixed) k_slr<n, float><<<g, b, 0, L.stream>>>(L.descs, L.count, arg_i);
-      else k_slr<n, double><<<g, b, 0, L.stream>>>(L.descs, L.count, arg_i);
+      if (qt32) k_slr<n, float, R><<<g, b, 0, L.stream>>>(L.descs, L.count, arg_i);
+      else k_slr<n, double, R><<<g, b, 0, L.stream>>>(L.descs, L.count, arg_i);
       break;
-    case PH_RELIN: k_relinearised<n><<<g, b, 0, L.stream>>>(L.descs, L.count); break;
-    case PH_SLR_FIN: k_slr_finish<n><<<g, b, 0, L.stream>>>(L.descs, L.count); break;
-    case PH_FINALIZE: k_finalize<n><<<g, b, 0, L.stream>>>(L.descs, L.count); break;
+    case PH_RELIN: k_relinearised<n, R><<<g, b, 0, L.stream>>>(L.descs, L.count); break;
+    case PH_SLR_FIN: k_slr_finish<n, R><<<g, b, 0, L.stream>>>(L.descs, L.count); break;
+    case PH_FINALIZE: k_finalize<n, R><<<g, b, 0, L.stream>>>(L.descs, L.count); break;
+    case PH_WORKING: k_working<n, R><<<g, b, 0, L.stream>>>(L.descs, L.count); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

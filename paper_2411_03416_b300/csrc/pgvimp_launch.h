@@ -1,21 +1,28 @@
 // pgvimp_launch.h -- launch groups of the hot-path kernels (internal).
 #pragma once
 #include "pgvimp_plan.h"
+#include "pgvimp_device.cuh"
 
 namespace pgv {
-template <int n, typename QT> cudaError_t launch_iter(const Launch& L, int iters);
-template <int n> cudaError_t launch_aux(const Launch& L, int phase, int arg_i, int mixed);
+template <int n, typename QT, typename R> cudaError_t launch_iter(const Launch& L, int iters);
+template <int n, typename R> cudaError_t launch_aux(const Launch& L, int phase, int arg_i, int qt32);
 template <int n> cudaError_t launch_rows(const Launch& L, int phase, double arg_d, int mixed);
-extern template cudaError_t launch_iter<4, float>(const Launch&, int);
-extern template cudaError_t launch_iter<4, double>(const Launch&, int);
-extern template cudaError_t launch_aux<4>(const Launch&, int, int, int);
+extern template cudaError_t launch_iter<4, float, double>(const Launch&, int);
+extern template cudaError_t launch_iter<4, double, double>(const Launch&, int);
+extern template cudaError_t launch_iter<4, float, df64>(const Launch&, int);
+extern template cudaError_t launch_aux<4, double>(const Launch&, int, int, int);
+extern template cudaError_t launch_aux<4, df64>(const Launch&, int, int, int);
 extern template cudaError_t launch_rows<4>(const Launch&, int, double, int);
-extern template cudaError_t launch_iter<6, float>(const Launch&, int);
-extern template cudaError_t launch_iter<6, double>(const Launch&, int);
-extern template cudaError_t launch_aux<6>(const Launch&, int, int, int);
+extern template cudaError_t launch_iter<6, float, double>(const Launch&, int);
+extern template cudaError_t launch_iter<6, double, double>(const Launch&, int);
+extern template cudaError_t launch_iter<6, float, df64>(const Launch&, int);
+extern template cudaError_t launch_aux<6, double>(const Launch&, int, int, int);
+extern template cudaError_t launch_aux<6, df64>(const Launch&, int, int, int);
 extern template cudaError_t launch_rows<6>(const Launch&, int, double, int);
-extern template cudaError_t launch_iter<14, float>(const Launch&, int);
-extern template cudaError_t launch_iter<14, double>(const Launch&, int);
-extern template cudaError_t launch_aux<14>(const Launch&, int, int, int);
+extern template cudaError_t launch_iter<14, float, double>(const Launch&, int);
+extern template cudaError_t launch_iter<14, double, double>(const Launch&, int);
+extern template cudaError_t launch_iter<14, float, df64>(const Launch&, int);
+extern template cudaError_t launch_aux<14, double>(const Launch&, int, int, int);
+extern template cudaError_t launch_aux<14, df64>(const Launch&, int, int, int);
 extern template cudaError_t launch_rows<14>(const Launch&, int, double, int);
 }  // namespace pgv

@@ -33,7 +33,8 @@ enum ScalSlot {
   S_T_DELTA = 13,     // delta^T Lambda_k delta of the last trial
   S_T_TRACE = 14,     // tr((Lambda_k - Lambda') Sigma') of the last trial
   S_T_BEST = 15,      // best-feasible buffer set during a search
-  S_NSETS = 16
+  S_NSETS = 16,
+  S_FMT = 17           // double-float storage: 1 while the result buffers hold FP64
 };
 
 struct PlanDesc;
