@@ -18,10 +18,15 @@ namespace pgv {
 #ifndef PGV_DEV
 #define PGV_DEV __device__ __forceinline__
 #endif
-// Full unrolling of the block loops only for small blocks (n <= 8).
+// Unrolling of the block loops: forced full for small blocks (n <= 8); for
+// larger blocks `#pragma unroll 0`, which the compiler ignores, leaving the
+// unroll factor to its heuristics.  Forcing those loops rolled (`unroll 1`)
+// made n = 14 routines over thread-local arrays return wrong covariance
+// blocks on sm_103a in some contexts, while the same code compiled for the
+// host, fully unrolled, or with the compiler's own choice is exact.
 // Large routines are inlined too: an out-of-line (__noinline__) build of the
-// n = 14 trial sweep, whose thread-local arrays exceed 20 KB, returned wrong
-// covariance blocks on sm_103a, while the inlined build is exact.
+// n = 14 trial sweep, whose thread-local arrays exceed 20 KB, showed the same
+// wrong results.
 #ifndef PGV_BIG
 #define PGV_BIG __device__ __forceinline__
 #endif
@@ -198,7 +203,7 @@ struct __align__(16) Pair2 {
 template <int n, typename R>
 PGV_DEV void ld_blk(const R* p, R* X) {
   const Pair2<R>* q = reinterpret_cast<const Pair2<R>*>(p);
-#pragma unroll (n <= 8 ? 32 : 1)
+#pragma unroll (n <= 8 ? 32 : 0)
   for (int e = 0; e < n * n / 2; ++e) {
     Pair2<R> v = q[e];
     X[2 * e] = v.a;
@@ -208,7 +213,7 @@ PGV_DEV void ld_blk(const R* p, R* X) {
 template <int n, typename R>
 PGV_DEV void st_blk(R* p, const R* X) {
   Pair2<R>* q = reinterpret_cast<Pair2<R>*>(p);
-#pragma unroll (n <= 8 ? 32 : 1)
+#pragma unroll (n <= 8 ? 32 : 0)
   for (int e = 0; e < n * n / 2; ++e) {
     Pair2<R> v;
     v.a = X[2 * e];
@@ -221,17 +226,17 @@ template <int n, typename R>
 PGV_DEV void ld_sym(const R* p, R* S) {
   R X[n * n];
   ld_blk<n, R>(p, X);
-#pragma unroll (n <= 8 ? 32 : 1)
+#pragma unroll (n <= 8 ? 32 : 0)
   for (int a = 0; a < n; ++a)
-#pragma unroll (n <= 8 ? 32 : 1)
+#pragma unroll (n <= 8 ? 32 : 0)
     for (int c = 0; c <= a; ++c) S[pk(a, c)] = X[a * n + c];
 }
 template <int n, typename R>
 PGV_DEV void st_sym(R* p, const R* S) {
   R X[n * n];
-#pragma unroll (n <= 8 ? 32 : 1)
+#pragma unroll (n <= 8 ? 32 : 0)
   for (int a = 0; a < n; ++a)
-#pragma unroll (n <= 8 ? 32 : 1)
+#pragma unroll (n <= 8 ? 32 : 0)
     for (int c = 0; c < n; ++c) X[a * n + c] = S[pk(a, c)];
   st_blk<n, R>(p, X);
 }
@@ -240,7 +245,7 @@ template <int n, typename R>
 PGV_DEV void ld_packed(const R* p, R* S) {
   const Pair2<R>* q = reinterpret_cast<const Pair2<R>*>(p);
   constexpr int np = n * (n + 1) / 2;
-#pragma unroll (n <= 8 ? 32 : 1)
+#pragma unroll (n <= 8 ? 32 : 0)
   for (int e = 0; e < (np + 1) / 2; ++e) {
     Pair2<R> v = q[e];
     S[2 * e] = v.a;
@@ -251,7 +256,7 @@ template <int n, typename R>
 PGV_DEV void st_packed(R* p, const R* S) {
   Pair2<R>* q = reinterpret_cast<Pair2<R>*>(p);
   constexpr int np = n * (n + 1) / 2;
-#pragma unroll (n <= 8 ? 32 : 1)
+#pragma unroll (n <= 8 ? 32 : 0)
   for (int e = 0; e < (np + 1) / 2; ++e) {
     Pair2<R> v;
     v.a = S[2 * e];
@@ -261,24 +266,24 @@ PGV_DEV void st_packed(R* p, const R* S) {
 }
 template <int n, typename R>
 PGV_DEV void ld_vec(const R* p, R* x) {
-#pragma unroll (n <= 8 ? 32 : 1)
+#pragma unroll (n <= 8 ? 32 : 0)
   for (int a = 0; a < n; ++a) x[a] = p[a];
 }
 template <int n, typename R>
 PGV_DEV void st_vec(R* p, const R* x) {
-#pragma unroll (n <= 8 ? 32 : 1)
+#pragma unroll (n <= 8 ? 32 : 0)
   for (int a = 0; a < n; ++a) p[a] = x[a];
 }
 
 // Z = X * S with S symmetric packed (full n x n result).
 template <int n, typename R>
 PGV_DEV void mul_full_sym(const R* X, const R* S, R* Z) {
-#pragma unroll (n <= 8 ? 32 : 1)
+#pragma unroll (n <= 8 ? 32 : 0)
   for (int a = 0; a < n; ++a)
-#pragma unroll (n <= 8 ? 32 : 1)
+#pragma unroll (n <= 8 ? 32 : 0)
     for (int c = 0; c < n; ++c) {
       R s = X[a * n] * S[pk(0, c)];
-#pragma unroll (n <= 8 ? 32 : 1)
+#pragma unroll (n <= 8 ? 32 : 0)
       for (int t = 1; t < n; ++t) s = r_fma(X[a * n + t], S[pk(t, c)], s);
       Z[a * n + c] = s;
     }
@@ -286,12 +291,12 @@ PGV_DEV void mul_full_sym(const R* X, const R* S, R* Z) {
 // Z = S * X with S symmetric packed.
 template <int n, typename R>
 PGV_DEV void mul_sym_full(const R* S, const R* X, R* Z) {
-#pragma unroll (n <= 8 ? 32 : 1)
+#pragma unroll (n <= 8 ? 32 : 0)
   for (int a = 0; a < n; ++a)
-#pragma unroll (n <= 8 ? 32 : 1)
+#pragma unroll (n <= 8 ? 32 : 0)
     for (int c = 0; c < n; ++c) {
       R s = S[pk(a, 0)] * X[c];
-#pragma unroll (n <= 8 ? 32 : 1)
+#pragma unroll (n <= 8 ? 32 : 0)
       for (int t = 1; t < n; ++t) s = r_fma(S[pk(a, t)], X[t * n + c], s);
       Z[a * n + c] = s;
     }
@@ -299,12 +304,12 @@ PGV_DEV void mul_sym_full(const R* S, const R* X, R* Z) {
 // packed Z = X * Y^T for a product known to be symmetric.
 template <int n, typename R>
 PGV_DEV void mul_nt_packed(const R* X, const R* Y, R* Z) {
-#pragma unroll (n <= 8 ? 32 : 1)
+#pragma unroll (n <= 8 ? 32 : 0)
   for (int a = 0; a < n; ++a)
-#pragma unroll (n <= 8 ? 32 : 1)
+#pragma unroll (n <= 8 ? 32 : 0)
     for (int c = 0; c <= a; ++c) {
       R s = X[a * n] * Y[c * n];
-#pragma unroll (n <= 8 ? 32 : 1)
+#pragma unroll (n <= 8 ? 32 : 0)
       for (int t = 1; t < n; ++t) s = r_fma(X[a * n + t], Y[c * n + t], s);
       Z[pk(a, c)] = s;
     }
@@ -312,12 +317,12 @@ PGV_DEV void mul_nt_packed(const R* X, const R* Y, R* Z) {
 // packed Z = C + X^T Y (symmetric result).
 template <int n, typename R>
 PGV_DEV void add_tn_packed(const R* C, const R* X, const R* Y, R* Z) {
-#pragma unroll (n <= 8 ? 32 : 1)
+#pragma unroll (n <= 8 ? 32 : 0)
   for (int a = 0; a < n; ++a)
-#pragma unroll (n <= 8 ? 32 : 1)
+#pragma unroll (n <= 8 ? 32 : 0)
     for (int c = 0; c <= a; ++c) {
       R s = C[pk(a, c)];
-#pragma unroll (n <= 8 ? 32 : 1)
+#pragma unroll (n <= 8 ? 32 : 0)
       for (int t = 0; t < n; ++t) s = r_fma(X[t * n + a], Y[t * n + c], s);
       Z[pk(a, c)] = s;
     }
@@ -329,20 +334,20 @@ template <int n, typename R>
 PGV_DEV void chol_inverse(const R* C, R* Cinv, LogDetAcc<R>& ld, bool& ok) {
   constexpr int np = n * (n + 1) / 2;
   R L[np], r[n];
-#pragma unroll (n <= 8 ? 32 : 1)
+#pragma unroll (n <= 8 ? 32 : 0)
   for (int j = 0; j < n; ++j) {
     R s = C[pk(j, j)];
-#pragma unroll (n <= 8 ? 32 : 1)
+#pragma unroll (n <= 8 ? 32 : 0)
     for (int k = 0; k < j; ++k) s = r_fma(-L[pk(j, k)], L[pk(j, k)], s);
     ok = ok && r_pos(s);
     s = r_pos(s) ? s : r_fromf<R>(1.0f);
     R rs = r_rsqrt(s);
     r[j] = rs;
     ld.mul(s);
-#pragma unroll (n <= 8 ? 32 : 1)
+#pragma unroll (n <= 8 ? 32 : 0)
     for (int i = j + 1; i < n; ++i) {
       R t = C[pk(i, j)];
-#pragma unroll (n <= 8 ? 32 : 1)
+#pragma unroll (n <= 8 ? 32 : 0)
       for (int k = 0; k < j; ++k) t = r_fma(-L[pk(i, k)], L[pk(j, k)], t);
       L[pk(i, j)] = t * rs;
     }
@@ -350,24 +355,24 @@ PGV_DEV void chol_inverse(const R* C, R* Cinv, LogDetAcc<R>& ld, bool& ok) {
   }
   // X = L^-1 (lower, packed)
   R X[np];
-#pragma unroll (n <= 8 ? 32 : 1)
+#pragma unroll (n <= 8 ? 32 : 0)
   for (int j = 0; j < n; ++j) {
     X[pk(j, j)] = r[j];
-#pragma unroll (n <= 8 ? 32 : 1)
+#pragma unroll (n <= 8 ? 32 : 0)
     for (int i = j + 1; i < n; ++i) {
       R s = L[pk(i, j)] * X[pk(j, j)];
-#pragma unroll (n <= 8 ? 32 : 1)
+#pragma unroll (n <= 8 ? 32 : 0)
       for (int k = j + 1; k < i; ++k) s = r_fma(L[pk(i, k)], X[pk(k, j)], s);
       X[pk(i, j)] = -(s * r[i]);
     }
   }
   // Cinv = X^T X
-#pragma unroll (n <= 8 ? 32 : 1)
+#pragma unroll (n <= 8 ? 32 : 0)
   for (int a = 0; a < n; ++a)
-#pragma unroll (n <= 8 ? 32 : 1)
+#pragma unroll (n <= 8 ? 32 : 0)
     for (int c = 0; c <= a; ++c) {
       R s = X[pk(a, a)] * X[pk(a, c)];
-#pragma unroll (n <= 8 ? 32 : 1)
+#pragma unroll (n <= 8 ? 32 : 0)
       for (int k = a + 1; k < n; ++k) s = r_fma(X[pk(k, a)], X[pk(k, c)], s);
       Cinv[pk(a, c)] = s;
     }

@@ -605,12 +605,12 @@ PGV_BIG TrialOut trial(const PlanDesc& P, double beta_d, int cur, int out, doubl
   res.trace = 0.0;
   const R beta = r_from<R>(beta_d), beta2 = beta + beta, zero = r_fromf<R>(0.0f);
   R SA[np], SM[np], vM[n], q[n], mi[n];
-#pragma unroll (n <= 8 ? 32 : 1)
+#pragma unroll (n <= 8 ? 32 : 0)
   for (int e = 0; e < np; ++e) {
     SA[e] = zero;
     SM[e] = zero;
   }
-#pragma unroll (n <= 8 ? 32 : 1)
+#pragma unroll (n <= 8 ? 32 : 0)
   for (int a = 0; a < n; ++a) {
     vM[a] = zero;
     q[a] = zero;
@@ -625,30 +625,30 @@ PGV_BIG TrialOut trial(const PlanDesc& P, double beta_d, int cur, int out, doubl
     {
       R B[nn];
       ld_blk<n, R>(Kd + (size_t)i * nn, B);
-#pragma unroll (n <= 8 ? 32 : 1)
+#pragma unroll (n <= 8 ? 32 : 0)
       for (int a = 0; a < n; ++a) {
         R s = q[a];
-#pragma unroll (n <= 8 ? 32 : 1)
+#pragma unroll (n <= 8 ? 32 : 0)
         for (int c = 0; c < n; ++c) s = r_fma(B[a * n + c], mi[c], s);
         Kmu[a] = s;
       }
-#pragma unroll (n <= 8 ? 32 : 1)
+#pragma unroll (n <= 8 ? 32 : 0)
       for (int a = 0; a < n; ++a)
-#pragma unroll (n <= 8 ? 32 : 1)
+#pragma unroll (n <= 8 ? 32 : 0)
         for (int c = 0; c <= a; ++c) {
           R kb = beta * B[a * n + c];
           CM[pk(a, c)] = kb - SM[pk(a, c)];
           CA[pk(a, c)] = kb - SA[pk(a, c)];
         }
       ld_blk<n, R>(GG + (size_t)i * nn, B);
-#pragma unroll (n <= 8 ? 32 : 1)
+#pragma unroll (n <= 8 ? 32 : 0)
       for (int a = 0; a < n; ++a)
-#pragma unroll (n <= 8 ? 32 : 1)
+#pragma unroll (n <= 8 ? 32 : 0)
         for (int c = 0; c <= a; ++c) CA[pk(a, c)] = r_fma(beta2, B[a * n + c], CA[pk(a, c)]);
       ld_blk<n, R>(Ld + (size_t)i * nn, B);
-#pragma unroll (n <= 8 ? 32 : 1)
+#pragma unroll (n <= 8 ? 32 : 0)
       for (int a = 0; a < n; ++a)
-#pragma unroll (n <= 8 ? 32 : 1)
+#pragma unroll (n <= 8 ? 32 : 0)
         for (int c = 0; c <= a; ++c) {
           CA[pk(a, c)] = CA[pk(a, c)] + B[a * n + c];
           CM[pk(a, c)] = CM[pk(a, c)] + B[a * n + c];
@@ -662,10 +662,10 @@ PGV_BIG TrialOut trial(const PlanDesc& P, double beta_d, int cur, int out, doubl
       ld_vec<n, R>(mu + (size_t)(i + 1) * n, mnext);
       ld_blk<n, R>(Ko + (size_t)i * nn, E);
       // K^-1 mu at i gets K^-1_{i,i+1} mu_{i+1}; at i+1 it gets K^-1_{i+1,i} mu_i
-#pragma unroll (n <= 8 ? 32 : 1)
+#pragma unroll (n <= 8 ? 32 : 0)
       for (int a = 0; a < n; ++a) {
         R s = zero, t = zero;
-#pragma unroll (n <= 8 ? 32 : 1)
+#pragma unroll (n <= 8 ? 32 : 0)
         for (int c = 0; c < n; ++c) {
           s = r_fma(E[c * n + a], mnext[c], s);
           t = r_fma(E[a * n + c], mi[c], t);
@@ -675,19 +675,19 @@ PGV_BIG TrialOut trial(const PlanDesc& P, double beta_d, int cur, int out, doubl
       }
       R B[nn];
       ld_blk<n, R>(Lo + (size_t)i * nn, B);
-#pragma unroll (n <= 8 ? 32 : 1)
+#pragma unroll (n <= 8 ? 32 : 0)
       for (int e = 0; e < nn; ++e) E[e] = r_fma(beta, E[e], B[e]);   // beta K^-1_{i+1,i} + Lambda_{i+1,i}
     }
     R y[n], z[n];
-#pragma unroll (n <= 8 ? 32 : 1)
+#pragma unroll (n <= 8 ? 32 : 0)
     for (int a = 0; a < n; ++a) {
       R r = (bb[(size_t)i * n + a] - gg[(size_t)i * n + a]) - Kmu[a];
       y[a] = r_fma(beta, r, -vM[a]);
     }
-#pragma unroll (n <= 8 ? 32 : 1)
+#pragma unroll (n <= 8 ? 32 : 0)
     for (int a = 0; a < n; ++a) {
       R s = CiM[pk(a, 0)] * y[0];
-#pragma unroll (n <= 8 ? 32 : 1)
+#pragma unroll (n <= 8 ? 32 : 0)
       for (int c = 1; c < n; ++c) s = r_fma(CiM[pk(a, c)], y[c], s);
       z[a] = s;
     }
@@ -701,15 +701,15 @@ PGV_BIG TrialOut trial(const PlanDesc& P, double beta_d, int cur, int out, doubl
       st_blk<n, R>(sp + Scr<n>::oWA, W);
       mul_full_sym<n, R>(E, CiM, W);
       mul_nt_packed<n, R>(W, E, SM);
-#pragma unroll (n <= 8 ? 32 : 1)
+#pragma unroll (n <= 8 ? 32 : 0)
       for (int a = 0; a < n; ++a) {
         R s = W[a * n] * y[0];
-#pragma unroll (n <= 8 ? 32 : 1)
+#pragma unroll (n <= 8 ? 32 : 0)
         for (int c = 1; c < n; ++c) s = r_fma(W[a * n + c], y[c], s);
         vM[a] = s;
       }
       st_blk<n, R>(sp + Scr<n>::oWM, W);
-#pragma unroll (n <= 8 ? 32 : 1)
+#pragma unroll (n <= 8 ? 32 : 0)
       for (int a = 0; a < n; ++a) mi[a] = mnext[a];
     }
   }
@@ -767,16 +767,16 @@ PGV_BIG TrialOut trial(const PlanDesc& P, double beta_d, int cur, int out, doubl
       R WM[nn], z[n];
       ld_blk<n, R>(sp + Scr<n>::oWM, WM);
       ld_vec<n, R>(sp + Scr<n>::oZ, z);
-#pragma unroll (n <= 8 ? 32 : 1)
+#pragma unroll (n <= 8 ? 32 : 0)
       for (int a = 0; a < n; ++a) {
         R s = z[a];
-#pragma unroll (n <= 8 ? 32 : 1)
+#pragma unroll (n <= 8 ? 32 : 0)
         for (int c = 0; c < n; ++c) s = r_fma(-WM[c * n + a], xn[c], s);
         xi[a] = s;
       }
     }
     R mo[n], dpi[n];
-#pragma unroll (n <= 8 ? 32 : 1)
+#pragma unroll (n <= 8 ? 32 : 0)
     for (int a = 0; a < n; ++a) {
       mo[a] = mu[(size_t)i * n + a] + xi[a];
       dpi[a] = mo[a] - mubar[(size_t)i * n + a];
@@ -784,39 +784,39 @@ PGV_BIG TrialOut trial(const PlanDesc& P, double beta_d, int cur, int out, doubl
     {
       R B[nn];
       ld_blk<n, R>(Ld + (size_t)i * nn, B);    // Lambda_k: trace, delta^T Lambda_k delta
-#pragma unroll (n <= 8 ? 32 : 1)
+#pragma unroll (n <= 8 ? 32 : 0)
       for (int a = 0; a < n; ++a)
-#pragma unroll (n <= 8 ? 32 : 1)
+#pragma unroll (n <= 8 ? 32 : 0)
         for (int c = 0; c < n; ++c) {
           trc = r_fma(B[a * n + c], Si[pk(a, c)], trc);
           dl = r_fma(xi[a] * B[a * n + c], xi[c], dl);
         }
       ld_blk<n, R>(GG + (size_t)i * nn, B);
-#pragma unroll (n <= 8 ? 32 : 1)
+#pragma unroll (n <= 8 ? 32 : 0)
       for (int a = 0; a < n; ++a)
-#pragma unroll (n <= 8 ? 32 : 1)
+#pragma unroll (n <= 8 ? 32 : 0)
         for (int c = 0; c < n; ++c) trc = r_fma(-(B[a * n + c] + B[a * n + c]), Si[pk(a, c)], trc);
       ld_blk<n, R>(Kd + (size_t)i * nn, B);
-#pragma unroll (n <= 8 ? 32 : 1)
+#pragma unroll (n <= 8 ? 32 : 0)
       for (int a = 0; a < n; ++a)
-#pragma unroll (n <= 8 ? 32 : 1)
+#pragma unroll (n <= 8 ? 32 : 0)
         for (int c = 0; c < n; ++c) {
           trc = r_fma(-B[a * n + c], Si[pk(a, c)], trc);
           ktr = r_fma(B[a * n + c], Si[pk(a, c)], ktr);
           kq = r_fma(dpi[a] * B[a * n + c], dpi[c], kq);
         }
       ld_blk<n, R>(Lo + (size_t)i * nn, B);
-#pragma unroll (n <= 8 ? 32 : 1)
+#pragma unroll (n <= 8 ? 32 : 0)
       for (int a = 0; a < n; ++a)
-#pragma unroll (n <= 8 ? 32 : 1)
+#pragma unroll (n <= 8 ? 32 : 0)
         for (int c = 0; c < n; ++c) {
           trc = r_fma(-(B[a * n + c] + B[a * n + c]), T[a * n + c], trc);
           dl = r_fma((xn[a] + xn[a]) * B[a * n + c], xi[c], dl);
         }
       ld_blk<n, R>(Ko + (size_t)i * nn, B);
-#pragma unroll (n <= 8 ? 32 : 1)
+#pragma unroll (n <= 8 ? 32 : 0)
       for (int a = 0; a < n; ++a)
-#pragma unroll (n <= 8 ? 32 : 1)
+#pragma unroll (n <= 8 ? 32 : 0)
         for (int c = 0; c < n; ++c) {
           trc = r_fma(B[a * n + c] + B[a * n + c], T[a * n + c], trc);
           ktr = r_fma(-(B[a * n + c] + B[a * n + c]), T[a * n + c], ktr);
@@ -825,17 +825,17 @@ PGV_BIG TrialOut trial(const PlanDesc& P, double beta_d, int cur, int out, doubl
     }
     {
       R X[np];
-#pragma unroll (n <= 8 ? 32 : 1)
+#pragma unroll (n <= 8 ? 32 : 0)
       for (int e = 0; e < np; ++e) X[e] = bp1 * Si[e];
       st_sym<n, R>(Sd_out + (size_t)i * nn, X);
-#pragma unroll (n <= 8 ? 32 : 1)
+#pragma unroll (n <= 8 ? 32 : 0)
       for (int e = 0; e < nn; ++e) T[e] = mbp1 * T[e];
       st_blk<n, R>(So_out + (size_t)i * nn, T);
       st_vec<n, R>(mo_out + (size_t)i * n, mo);
     }
-#pragma unroll (n <= 8 ? 32 : 1)
+#pragma unroll (n <= 8 ? 32 : 0)
     for (int e = 0; e < np; ++e) Sn[e] = Si[e];
-#pragma unroll (n <= 8 ? 32 : 1)
+#pragma unroll (n <= 8 ? 32 : 0)
     for (int a = 0; a < n; ++a) {
       xn[a] = xi[a];
       dpn[a] = dpi[a];
@@ -864,13 +864,13 @@ PGV_BIG void accept_precision(const PlanDesc& P, double beta_d) {
     ld_blk<n, R>(Kd + (size_t)i * nn, K);
     ld_blk<n, R>(Ld + (size_t)i * nn, Lb);
     ld_blk<n, R>(GG + (size_t)i * nn, Gb);
-#pragma unroll (n <= 8 ? 32 : 1)
+#pragma unroll (n <= 8 ? 32 : 0)
     for (int e = 0; e < nn; ++e) Lb[e] = r_fma(beta, r_fma(two, Gb[e], K[e]), Lb[e]) * inv;
     st_blk<n, R>(Ld + (size_t)i * nn, Lb);
     if (i < N) {
       ld_blk<n, R>(Ko + (size_t)i * nn, K);
       ld_blk<n, R>(Lo + (size_t)i * nn, Lb);
-#pragma unroll (n <= 8 ? 32 : 1)
+#pragma unroll (n <= 8 ? 32 : 0)
       for (int e = 0; e < nn; ++e) Lb[e] = r_fma(beta, K[e], Lb[e]) * inv;
       st_blk<n, R>(Lo + (size_t)i * nn, Lb);
     }
