@@ -282,12 +282,16 @@ def kernel_only(args):
     b.close()
 
 
+DTYPES = {0: "f64", 1: "f32 quadrature + f64 recursions",
+          2: "f32 quadrature + double-float (f32 pair) recursions"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--batch", type=int, default=4736, help="plans per GPU (one thread each)")
+    ap.add_argument("--batch", type=int, default=37888, help="plans per GPU (one thread each; 37,888 = 8 warps per SM)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--plain-steps", type=int, default=2)
@@ -430,7 +434,7 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": "plans/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1000.0 * t_max / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32 quadrature + f64 recursions", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": DTYPES[head], "data": "synthetic",
         "config": config_dict(args.batch, ws),
         "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
                        "note": "batch latency: every plan of a step completes at the end of the step"},

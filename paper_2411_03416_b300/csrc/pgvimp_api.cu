@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -240,6 +241,7 @@ struct PlanLayout {
   size_t mu0_, Sd0, So0, Ld, Lo;                                  // OUTPUT (per plan)
   size_t Kd, Ko, b, mubar, mu1, Sd1, So1, mu2, Sd2, So2, g, G, Altv, altv, xbar, scr;  // WORK
   size_t A_cnt, a_cnt, sdf_cnt;
+  bool sdf_owner;   // false: the grid is shared with an earlier plan of the batch
   int log_cap, slr_cap;
 };
 
@@ -294,6 +296,9 @@ void plan_layout(BatchImpl& B) {
   res = align256(res + sizeof(double) * (size_t)slr_cap * cnt);
   size_t extra = 0, work = 0;
   B.lay.resize(cnt);
+  // Plans that pass the same host grid (same pointer and size) share one
+  // device copy: maps are read-only and a batch often reuses a few of them.
+  std::map<std::pair<const float*, size_t>, size_t> sdf_seen;
   for (int i = 0; i < cnt; ++i) {
     const pgvimp_problem& p = B.probs[i];
     PlanLayout& L = B.lay[i];
@@ -321,7 +326,20 @@ void plan_layout(BatchImpl& B) {
     L.dh = take(in, 8 * std::max<size_t>(4 * dof, 1));
     L.soff = take(in, 8 * std::max<size_t>(3 * S, 1));
     L.srad = take(in, 8 * std::max<size_t>(S, 1));
-    L.sdf = take(in, 4 * std::max<size_t>(L.sdf_cnt, 1));
+    L.sdf_owner = true;
+    if (L.sdf_cnt) {
+      auto key = std::make_pair(p.sdf, L.sdf_cnt);
+      auto it = sdf_seen.find(key);
+      if (it != sdf_seen.end()) {
+        L.sdf = it->second;
+        L.sdf_owner = false;
+      } else {
+        L.sdf = take(in, 4 * L.sdf_cnt);
+        sdf_seen.emplace(key, L.sdf);
+      }
+    } else {
+      L.sdf = take(in, 4);
+    }
     L.mu0_ = take(res, 8 * (N + 1) * n);
     L.Sd0 = take(res, 8 * (N + 1) * nn);
     L.So0 = take(extra, 8 * N * nn);
@@ -453,7 +471,7 @@ void stage_inputs(BatchImpl& B) {
             ++c;
           }
     }
-    if (L.sdf_cnt) std::memcpy(h + L.sdf, p.sdf, 4 * L.sdf_cnt);
+    if (L.sdf_cnt && L.sdf_owner) std::memcpy(h + L.sdf, p.sdf, 4 * L.sdf_cnt);
   }
 }
 

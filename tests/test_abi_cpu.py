@@ -89,3 +89,24 @@ def test_validation_rejects_bad_inputs(pg):
     bad_sdf[3, 3] = np.inf
     assert _arena_status(pg, replace(pb, sdf=bad_sdf), op)[0] == _lib.ENOTFINITE
     assert _arena_status(pg, pb, op, precision=7)[0] == _lib.EINVAL
+
+
+def test_plans_sharing_a_map_store_it_once(pg):
+    """Plans that pass the same grid share one device copy of it; distinct
+    grids with equal contents are still stored separately."""
+    from paper_2411_03416_b300 import _lib
+    pb, op = W.c1_point2d()
+    keep = _lib._Keep()
+
+    def arena(probs):
+        parr = (_lib.Problem * len(probs))(*[_lib.marshal_problem(p, keep) for p in probs])
+        oarr = (_lib.Options * len(probs))(*[_lib.marshal_options(op) for _ in probs])
+        nb = C.c_size_t(0)
+        assert pg.lib().pgvimp_batch_arena_bytes(len(probs), C.cast(parr, C.c_void_p), C.cast(oarr, C.c_void_p),
+                                                 1, C.byref(nb)) == 0
+        return nb.value
+
+    grid = pb.sdf.nbytes
+    shared = arena([pb, replace(pb, muN=pb.muN + 0.1)])
+    separate = arena([pb, replace(pb, sdf=np.array(pb.sdf, copy=True))])
+    assert separate - shared >= grid

@@ -161,6 +161,18 @@ def test_batch_equals_alone_and_ragged(pg, prec):
         np.testing.assert_array_equal(together[i].Sd, alone.Sd)
 
 
+def test_plans_sharing_a_map(pg):
+    """Plans that pass the same grid object share its device copy; each
+    result still equals the plan run alone."""
+    pb, op = W.c1_point2d(N=40, iters=6)
+    probs = [replace(pb, muN=pb.muN + np.array([0.3 * k, -0.2 * k, 0.0, 0.0])) for k in range(4)]
+    together = gpu_solve(probs, [op] * 4, MIXED)
+    for i, p in enumerate(probs):
+        alone = gpu_solve([p], [op], MIXED)[0]
+        np.testing.assert_array_equal(together[i].mu, alone.mu)
+        np.testing.assert_array_equal(together[i].Sd, alone.Sd)
+
+
 def test_context_api_matches_batch(pg):
     pb, op = W.c1_point2d(N=20, iters=5)
     from paper_2411_03416_b300 import Context
