@@ -226,6 +226,33 @@ pgvimp_status pgvimp_destroy(pgvimp_ctx *ctx);
 /* Last error text of a context (or of the calling thread if ctx is NULL). */
 const char *pgvimp_last_error(const void *ctx);
 
+/* ----------------------------------------------- allocation-free marginals
+ * The paper has no counterpart to this entry point; it serves callers that
+ * cannot allocate device memory -- code running while its stream is captured
+ * into a CUDA graph (cudaMalloc is not capturable and may synchronise the
+ * device), runtimes that give a component a fixed memory budget, hosts that
+ * own every device byte through their own pool.  It computes the block
+ * marginals of a block-tridiagonal SPD precision like PGVIMP_PHASE_MARGINALS
+ * (same elimination and selected-inverse sweeps, FP64), but the per-state
+ * scratch lives in a fixed device array of 4 MiB compiled into the library,
+ * which every GPU that loads the library holds until the process exits.
+ *   n: 4, 6 or 14; N >= 1 with (N+1) * (n(n+1)/2 rounded up to even + n*n)
+ *      * 8 bytes <= 4 MiB (n = 4: N <= 20,163; n = 6: N <= 9,038; n = 14: N <= 1,735);
+ *      larger sizes return PGVIMP_EINVAL;
+ *   Ld, Lo: device input blocks ((N+1) n*n, N n*n); Sd, So: device outputs
+ *      (Sigma_ii, Sigma_{i+1,i}); the four 16-byte aligned; logdet: device,
+ *      one double (NaN when the precision is not positive definite, in which
+ *      case Sd / So are not written).  The caller owns all five buffers.
+ * The call allocates nothing and returns after queueing one kernel on
+ * `stream`.  Its first call on a device resolves the array's device address
+ * (cudaGetSymbolAddress) and should come before any stream capture.  All
+ * calls share the array: calls that overlap on the GPU race on it, so the
+ * caller serialises them (one stream, or events).  Errors: PGVIMP_EINVAL for
+ * bad sizes or pointers, PGVIMP_ECUDA for a failed launch; the text is
+ * available from pgvimp_last_error(NULL). */
+pgvimp_status pgvimp_marginals_noalloc(int n, int N, const double *Ld, const double *Lo, double *Sd, double *So,
+                                       double *logdet, void *stream);
+
 /* Library build / device information: writes a short text (e.g. "sm_103a"). */
 pgvimp_status pgvimp_version(char *buf, size_t len);
 

@@ -31,7 +31,7 @@ EXPORTED = [
     "pgvimp_batch_io_bytes",
     "pgvimp_batch_destroy", "pgvimp_batch_phase", "pgvimp_batch_read", "pgvimp_batch_write",
     "pgvimp_create", "pgvimp_step", "pgvimp_plan", "pgvimp_get", "pgvimp_destroy", "pgvimp_last_error",
-    "pgvimp_version", "pgvimp_abi_sizes",
+    "pgvimp_version", "pgvimp_abi_sizes", "pgvimp_marginals_noalloc",
 ]
 
 
@@ -108,6 +108,7 @@ def lib():
     L.pgvimp_get.argtypes = [C.c_void_p] + [C.c_void_p] * 4
     L.pgvimp_destroy.argtypes = [C.c_void_p]
     L.pgvimp_version.argtypes = [C.c_char_p, C.c_size_t]
+    L.pgvimp_marginals_noalloc.argtypes = [C.c_int, C.c_int] + [C.c_void_p] * 6
     _lib = L
     return L
 
@@ -339,6 +340,15 @@ class Context:
             self.close()
         except Exception:
             pass
+
+
+def marginals_noalloc(n: int, N: int, Ld, Lo, Sd, So, logdet, stream=None):
+    """pgvimp_marginals_noalloc on CUDA tensors (float64, contiguous): block
+    marginals of (Ld, Lo) into (Sd, So) and log det into `logdet` (1 element),
+    with no device allocation by the library."""
+    _check(lib().pgvimp_marginals_noalloc(n, N, C.c_void_p(Ld.data_ptr()), C.c_void_p(Lo.data_ptr()),
+                                          C.c_void_p(Sd.data_ptr()), C.c_void_p(So.data_ptr()),
+                                          C.c_void_p(logdet.data_ptr()), _stream_handle(stream)))
 
 
 def version() -> str:

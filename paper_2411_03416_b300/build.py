@@ -17,7 +17,7 @@ OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libpgvimp.so")
 ROOT = os.path.dirname(HERE)
 
-SOURCES = ["pgvimp_api.cu"] + [f"k{n}_{part}.cu" for n in (6, 4, 14)
+SOURCES = ["pgvimp_api.cu", "pgvimp_noalloc.cu"] + [f"k{n}_{part}.cu" for n in (6, 4, 14)
                                for part in ("iter_df", "iter_f32", "iter_f64", "aux", "aux_df", "rows")]
 HEADERS = ["pgvimp_device.cuh", "pgvimp_kernels.cuh", "pgvimp_plan.h", "pgvimp_launch.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

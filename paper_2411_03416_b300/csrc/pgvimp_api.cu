@@ -41,11 +41,15 @@ static cudaError_t launch_phase(int n, const Launch& L, int phase, int arg_i, do
 }
 }  // namespace pgv
 
+namespace {
+thread_local std::string g_thread_error;
+}  // namespace
+
+void pgv::set_thread_error(const char* msg) { g_thread_error = msg ? msg : ""; }
+
 using namespace pgv;
 
 namespace {
-
-thread_local std::string g_thread_error;
 
 pgvimp_status fail(std::string* where, pgvimp_status st, const std::string& msg) {
   g_thread_error = msg;

@@ -5,6 +5,8 @@
 #include <stdint.h>
 #include <cuda_runtime.h>
 
+#include <string>
+
 #include "../../include/pgvimp.h"
 
 namespace pgv {
@@ -36,6 +38,10 @@ enum ScalSlot {
   S_NSETS = 16,
   S_FMT = 17           // double-float storage: 1 while the result buffers hold FP64
 };
+
+// Sets the calling thread's error text returned by pgvimp_last_error(NULL).
+void set_thread_error(const char* msg);
+inline void set_thread_error(const std::string& msg) { set_thread_error(msg.c_str()); }
 
 struct PlanDesc;
 struct Launch {
