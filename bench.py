@@ -246,6 +246,115 @@ def config_dict(batch, ws):
             "l2": "inputs larger than L2 (no flush needed)", "parallelism": f"replicas x{ws}"}
 
 
+# ------------------------------------------------------------------- serving
+
+SERVE_BUDGET = 80 << 30   # HBM admission budget of the serving mix
+
+
+def _pct(v, q):
+    import numpy as np
+    return float(np.percentile(np.asarray(v, dtype=float), q)) if len(v) else None
+
+
+def run_served(mix, precision, plan_threads, max_inflight=16, max_batch=32, window_ms=2.0):
+    """Replays the mix's arrival times against a server (continuous batching)
+    and returns plans/s (count / time from the first arrival to the last
+    result on the host) and p50/p99 latency (arrival to result on the host)."""
+    import threading
+
+    import paper_2411_03416_b300 as pg
+    srv = pg.Server(SERVE_BUDGET, precision=precision, plan_threads=plan_threads, max_inflight=max_inflight,
+                    max_batch=max_batch, batch_window_ms=window_ms)
+    seen = set()
+    for rq in mix:                          # load every kernel the mix uses before timing
+        key = (rq.problem.n, rq.problem.dyn_kind)
+        if key not in seen:
+            seen.add(key)
+            srv.poll(srv.submit(rq.problem, rq.options))
+    ids = [None] * len(mix)
+    lags = []
+    t0 = time.perf_counter()
+    s0 = srv.stats()["now_ms"]
+
+    def submitter():
+        for k, rq in enumerate(mix):
+            d = t0 + rq.arrival_s - time.perf_counter()
+            if d > 0:
+                time.sleep(d)
+            ids[k] = srv.submit(rq.problem, rq.options)
+            lags.append(time.perf_counter() - t0 - rq.arrival_s)
+
+    th = threading.Thread(target=submitter)
+    th.start()
+    lat, done, sizes = [], [], []
+    for k, rq in enumerate(mix):
+        while ids[k] is None:
+            time.sleep(1e-4)
+        _, _, info = srv.poll(ids[k], timeout_ms=-1)
+        lat.append(info["done_ms"] - (s0 + 1000.0 * rq.arrival_s))
+        done.append(info["done_ms"] - s0)
+        sizes.append(info["batch_size"])
+    th.join()
+    st = srv.stats()
+    srv.close()
+    span_s = max(done) / 1000.0
+    return {"plans_per_s": len(mix) / span_s, "p50_ms": _pct(lat, 50), "p99_ms": _pct(lat, 99),
+            "makespan_s": span_s, "requests": len(mix), "batches": st["batches"] - len(seen),
+            "mean_batch": sum(sizes) / len(sizes), "submit_lag_ms_max": 1000.0 * max(lags),
+            "precision": precision, "plan_threads": plan_threads, "max_inflight": max_inflight,
+            "max_batch": max_batch, "batch_window_ms": window_ms}
+
+
+def run_plain(mix, plan_threads):
+    """Plain per-request FP64: one plan at a time through the single-plan calls
+    (pgvimp_create / plan / get / destroy) on one stream, no batching, in
+    arrival order; latency from arrival to the result on the host."""
+    from dataclasses import replace
+
+    import paper_2411_03416_b300 as pg
+    from paper_2411_03416_b300 import _lib as L
+    seen = set()
+    for rq in mix:
+        key = (rq.problem.n, rq.problem.dyn_kind)
+        if key not in seen:
+            seen.add(key)
+            c = pg.Context(rq.problem, replace(rq.options, plan_threads=plan_threads), L.PREC_PLAIN_FP64)
+            c.plan()
+            c.get()
+            c.close()
+    lat = []
+    t0 = time.perf_counter()
+    for rq in mix:
+        d = t0 + rq.arrival_s - time.perf_counter()
+        if d > 0:
+            time.sleep(d)
+        c = pg.Context(rq.problem, replace(rq.options, plan_threads=plan_threads), L.PREC_PLAIN_FP64)
+        c.plan()
+        c.get()
+        c.close()
+        lat.append(1000.0 * (time.perf_counter() - t0 - rq.arrival_s))
+    span_s = time.perf_counter() - t0
+    return {"plans_per_s": len(mix) / span_s, "p50_ms": _pct(lat, 50), "p99_ms": _pct(lat, 99),
+            "makespan_s": span_s, "requests": len(mix), "precision": 0, "plan_threads": plan_threads}
+
+
+def serving(args):
+    import workloads as W
+    mix = W.c5_mix(args.serve_count)
+    out = {"workload": f"serving mix: {args.serve_count} requests, Poisson arrivals at 2000/s; 50% 2-D point robot "
+                       "N~U{50..1000}, 30% planar quadrotor SLR N~U{100..500}, 20% 7-DOF arm N~U{100..300}; "
+                       "own seeded map per request; 80 GB admission budget",
+           "latency": "arrival to result on the host (server clock)"}
+    # served FP32/FP64: FP32 quadrature, FP64 recursions, block form, continuous batching
+    out["served_fp32_fp64"] = run_served(mix, 1, args.serve_threads)
+    out["served_plain_fp64"] = run_served(mix, 0, args.serve_threads)
+    sample = mix[:args.plain_count]
+    out["plain_sample"] = f"first {len(sample)} requests of the mix (arrival times kept)"
+    out["plain_fp64_per_request"] = run_plain(sample, args.serve_threads)
+    out["served_fp32_fp64_on_sample"] = run_served(sample, 1, args.serve_threads)
+    return out
+
+
 PRECISIONS = {"fp64": 0, "mixed": 1, "mixed_df": 2}
 DTYPES = {0: "f64", 1: "f32 quadrature + f64 recursions",
           2: "f32 quadrature + double-float (f32-pair, ~48-bit) recursions"}
@@ -299,6 +408,9 @@ def main():
     ap.add_argument("--kernel-only", action="store_true",
                     help="profiling target: prior phase, then one fused-iteration launch; no JSON line")
     ap.add_argument("--iters", type=int, default=ITERS, help="proximal iterations (kernel-only mode)")
+    ap.add_argument("--serve-count", type=int, default=512, help="requests of the serving mix (0: skip serving)")
+    ap.add_argument("--plain-count", type=int, default=32, help="requests of the plain per-request FP64 sample")
+    ap.add_argument("--serve-threads", type=int, default=64, help="threads per plan in the served block form")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -429,6 +541,8 @@ def main():
         if head != L.PREC_MIXED_DF:
             others["served_double_float_recursions"] = time_steps(L.PREC_MIXED_DF, args.plain_steps)
 
+    serve = serving(args) if (args.serve_count > 0 and rank == 0) else None
+
     if rank != 0:
         return
     line = {
@@ -445,6 +559,7 @@ def main():
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": "plans/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "ms_per_step": statistics.median(e2e_ms)},
+        "serving": serve,
         "clocks": clk.summary(),
         "gpu_launches": 4 * args.steps,
         "wall_s_timed": t_wall,

@@ -118,6 +118,11 @@ typedef struct {
   int slr_iters;    /* SLR linearisations (Alg. 2); ignored for LINEAR */
   int init_kind;    /* 0: Lambda_0 = K^-1; 1: Lambda_0 = init_scale * I */
   double init_scale;
+  int plan_threads; /* execution form (same for every plan of a batch; not part of the method):
+                       0 or 1: one GPU thread per plan, sequential sweeps over time (throughput form);
+                       32..256, a multiple of 32: one thread block of that size per plan, the block
+                       recursions by cyclic reduction over time (latency form); PLAIN_FP64 or MIXED
+                       precision only (EINVAL with MIXED_DF). */
 } pgvimp_options;
 
 /* Per-iteration record.  Costs are those of the iterate the gradients were
@@ -225,6 +230,57 @@ pgvimp_status pgvimp_destroy(pgvimp_ctx *ctx);
 
 /* Last error text of a context (or of the calling thread if ctx is NULL). */
 const char *pgvimp_last_error(const void *ctx);
+
+/* ------------------------------------------------------------------ serving
+ * A server plans requests as they arrive (continuous batching).  Requests of
+ * the same state dimension and dynamics kind that wait at the same time are
+ * packed into one batch; each batch runs the whole plan (Alg. 1, or Alg. 2
+ * for SLR models) on one of `max_inflight` streams, so batches admitted while
+ * others run overlap on the GPU.  A batch is admitted when a stream is free
+ * and its device arena and pinned staging fit the server's pools, which are
+ * allocated once at creation; a request waits at most `batch_window_ms` for
+ * others to share its launch.  All server functions are thread-safe. */
+typedef struct pgvimp_server pgvimp_server;
+typedef struct {
+  size_t hbm_budget_bytes;   /* device pool for admitted batches (>= 1 MiB) */
+  size_t host_staging_bytes; /* pinned host pool (0: min(hbm_budget_bytes, 4 GiB)) */
+  int precision;             /* pgvimp_precision of every served plan */
+  int plan_threads;          /* execution form of every served plan (pgvimp_options.plan_threads) */
+  int max_inflight;          /* batches on the device at once, 1..64 */
+  int max_batch;             /* plans per batch, >= 1 */
+  double batch_window_ms;    /* longest wait of a queued request for batch company, >= 0 */
+} pgvimp_server_config;
+typedef struct {
+  int status;                /* pgvimp_status of the plan */
+  int n, N, n_logs;          /* sizes and number of iteration records */
+  int batch_size;            /* plans in the batch that carried the request */
+  double submit_ms, start_ms, done_ms;   /* server clock: submitted, launched, result on the host */
+  pgvimp_step_info last;     /* last iteration record */
+} pgvimp_request_info;
+typedef struct {
+  int queued, inflight;      /* requests waiting, batches on the device */
+  uint64_t batches, plans;   /* launched so far */
+  size_t dev_used, host_used;
+  double now_ms;             /* server clock */
+} pgvimp_server_stats_t;
+
+/* Creates the pools, streams and the scheduler thread on the current device.
+ * EINVAL for a bad config, ENOMEM if a pool cannot be allocated. */
+pgvimp_status pgvimp_server_create(const pgvimp_server_config *cfg, pgvimp_server **out);
+/* Validates and deep-copies one request (the caller may free its arrays on
+ * return) and queues it.  options.plan_threads is replaced by the server's.
+ * ENOMEM if the request alone exceeds a pool; validation as pgvimp_batch_create. */
+pgvimp_status pgvimp_submit(pgvimp_server *s, const pgvimp_problem *problem, const pgvimp_options *options,
+                            uint64_t *request_id);
+/* Waits up to timeout_ms (< 0: no limit, 0: no wait) for a request; on
+ * completion copies mu ((N+1) n) and Sigma ((N+1) n n; either may be NULL),
+ * fills info (may be NULL), forgets the request and returns the plan's status.
+ * ENOTREADY if it has not finished (the request stays queued). */
+pgvimp_status pgvimp_poll(pgvimp_server *s, uint64_t request_id, int timeout_ms, double *mu, double *Sigma,
+                          pgvimp_request_info *info);
+pgvimp_status pgvimp_server_stats(pgvimp_server *s, pgvimp_server_stats_t *out);
+/* Waits for the batches on the device, drops queued requests, frees everything. NULL-safe. */
+pgvimp_status pgvimp_server_destroy(pgvimp_server *s);
 
 /* ----------------------------------------------- allocation-free marginals
  * The paper has no counterpart to this entry point; it serves callers that

@@ -6,8 +6,9 @@ quadrature, gradient assembly, the KL-proximal update with its step-size
 search, and the SLR outer loop -- runs in hand-written CUDA kernels behind the
 C ABI in include/pgvimp.h; this package is its thin ctypes binding.
 """
-from ._lib import (PREC_MIXED, PREC_MIXED_DF, PREC_PLAIN_FP64, Batch, Context, PgvimpError, PlanResult, lib, solve,  # noqa: F401
+from ._lib import (PREC_MIXED, PREC_MIXED_DF, PREC_PLAIN_FP64, Batch, Context, PgvimpError, PlanResult, Server,  # noqa: F401
+                   lib, solve,
                    version)
 
-__all__ = ["Batch", "Context", "PgvimpError", "PlanResult", "PREC_MIXED", "PREC_MIXED_DF", "PREC_PLAIN_FP64", "lib", "solve",
+__all__ = ["Batch", "Context", "PgvimpError", "PlanResult", "PREC_MIXED", "PREC_MIXED_DF", "PREC_PLAIN_FP64", "Server", "lib", "solve",
            "version"]

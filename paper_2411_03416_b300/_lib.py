@@ -32,6 +32,7 @@ EXPORTED = [
     "pgvimp_batch_destroy", "pgvimp_batch_phase", "pgvimp_batch_read", "pgvimp_batch_write",
     "pgvimp_create", "pgvimp_step", "pgvimp_plan", "pgvimp_get", "pgvimp_destroy", "pgvimp_last_error",
     "pgvimp_version", "pgvimp_abi_sizes", "pgvimp_marginals_noalloc",
+    "pgvimp_server_create", "pgvimp_submit", "pgvimp_poll", "pgvimp_server_stats", "pgvimp_server_destroy",
 ]
 
 
@@ -61,7 +62,7 @@ class Options(C.Structure):
     _fields_ = [
         ("rule", C.c_int), ("gh_p", C.c_int), ("beta_max", C.c_double), ("kl_eps", C.c_double),
         ("max_bisect", C.c_int), ("iters", C.c_int), ("slr_iters", C.c_int), ("init_kind", C.c_int),
-        ("init_scale", C.c_double),
+        ("init_scale", C.c_double), ("plan_threads", C.c_int),
     ]
 
 
@@ -70,6 +71,28 @@ class StepInfo(C.Structure):
         ("beta", C.c_double), ("kl", C.c_double), ("kl_margin", C.c_double),
         ("prior_cost", C.c_double), ("collision_cost", C.c_double), ("entropy", C.c_double),
         ("trials", C.c_int), ("iter", C.c_int),
+    ]
+
+
+class ServerConfig(C.Structure):
+    _fields_ = [
+        ("hbm_budget_bytes", C.c_size_t), ("host_staging_bytes", C.c_size_t), ("precision", C.c_int),
+        ("plan_threads", C.c_int), ("max_inflight", C.c_int), ("max_batch", C.c_int),
+        ("batch_window_ms", C.c_double),
+    ]
+
+
+class RequestInfo(C.Structure):
+    _fields_ = [
+        ("status", C.c_int), ("n", C.c_int), ("N", C.c_int), ("n_logs", C.c_int), ("batch_size", C.c_int),
+        ("submit_ms", C.c_double), ("start_ms", C.c_double), ("done_ms", C.c_double), ("last", StepInfo),
+    ]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [
+        ("queued", C.c_int), ("inflight", C.c_int), ("batches", C.c_uint64), ("plans", C.c_uint64),
+        ("dev_used", C.c_size_t), ("host_used", C.c_size_t), ("now_ms", C.c_double),
     ]
 
 
@@ -109,6 +132,11 @@ def lib():
     L.pgvimp_destroy.argtypes = [C.c_void_p]
     L.pgvimp_version.argtypes = [C.c_char_p, C.c_size_t]
     L.pgvimp_marginals_noalloc.argtypes = [C.c_int, C.c_int] + [C.c_void_p] * 6
+    L.pgvimp_server_create.argtypes = [C.c_void_p, C.POINTER(C.c_void_p)]
+    L.pgvimp_submit.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_uint64)]
+    L.pgvimp_poll.argtypes = [C.c_void_p, C.c_uint64, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]
+    L.pgvimp_server_stats.argtypes = [C.c_void_p, C.c_void_p]
+    L.pgvimp_server_destroy.argtypes = [C.c_void_p]
     _lib = L
     return L
 
@@ -177,6 +205,7 @@ def marshal_options(op) -> Options:
     o.rule, o.gh_p, o.beta_max, o.kl_eps = op.rule, op.gh_p, op.beta_max, op.kl_eps
     o.max_bisect, o.iters, o.slr_iters = op.max_bisect, op.iters, op.slr_iters
     o.init_kind, o.init_scale = op.init_kind, op.init_scale
+    o.plan_threads = getattr(op, "plan_threads", 0)
     return o
 
 
@@ -333,6 +362,62 @@ class Context:
     def close(self):
         if getattr(self, "h", None):
             lib().pgvimp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """The serving calls (pgvimp_server_create / submit / poll / destroy):
+    continuous batching of independent plan requests on one GPU."""
+
+    def __init__(self, hbm_budget_bytes: int, precision: int = PREC_MIXED, plan_threads: int = 64,
+                 max_inflight: int = 16, max_batch: int = 32, batch_window_ms: float = 2.0,
+                 host_staging_bytes: int = 0):
+        cfg = ServerConfig(hbm_budget_bytes, host_staging_bytes, precision, plan_threads, max_inflight, max_batch,
+                           batch_window_ms)
+        h = C.c_void_p()
+        _check(lib().pgvimp_server_create(C.byref(cfg), C.byref(h)))
+        self.h = h
+        self._sizes = {}
+
+    def submit(self, problem, options) -> int:
+        keep = _Keep()
+        p = marshal_problem(problem, keep)
+        o = marshal_options(options)
+        rid = C.c_uint64(0)
+        _check(lib().pgvimp_submit(self.h, C.byref(p), C.byref(o), C.byref(rid)))
+        self._sizes[rid.value] = (problem.n, problem.N)
+        return rid.value
+
+    def poll(self, rid: int, timeout_ms: int = -1):
+        """(mu, Sigma_ii, info) once the request is done; None if it is not
+        finished within timeout_ms; raises PgvimpError if the plan failed."""
+        n, N = self._sizes[rid]
+        mu, Sd = np.zeros((N + 1, n)), np.zeros((N + 1, n, n))
+        info = RequestInfo()
+        st = lib().pgvimp_poll(self.h, rid, timeout_ms, _p(mu), _p(Sd), C.byref(info))
+        if st == ENOTREADY:
+            return None
+        del self._sizes[rid]
+        _check(st)
+        d = {k: getattr(info, k) for k in ("status", "n", "N", "n_logs", "batch_size", "submit_ms", "start_ms",
+                                           "done_ms")}
+        d["last"] = _log_dicts([info.last], 1)[0]
+        return mu, Sd, d
+
+    def stats(self) -> dict:
+        s = ServerStats()
+        _check(lib().pgvimp_server_stats(self.h, C.byref(s)))
+        return {k: getattr(s, k) for k, _ in ServerStats._fields_}
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().pgvimp_server_destroy(self.h)
             self.h = None
 
     def __del__(self):

@@ -17,9 +17,11 @@ OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libpgvimp.so")
 ROOT = os.path.dirname(HERE)
 
-SOURCES = ["pgvimp_api.cu", "pgvimp_noalloc.cu"] + [f"k{n}_{part}.cu" for n in (6, 4, 14)
-                               for part in ("iter_df", "iter_f32", "iter_f64", "aux", "aux_df", "rows")]
-HEADERS = ["pgvimp_device.cuh", "pgvimp_kernels.cuh", "pgvimp_plan.h", "pgvimp_launch.h"]
+SOURCES = ["pgvimp_api.cu", "pgvimp_noalloc.cu", "pgvimp_server.cu"] + [f"k{n}_{part}.cu" for n in (14, 6, 4)
+                               for part in ("iter_df", "iter_f32", "cta_f32", "iter_f64", "cta_f64",
+                                            "aux", "aux_df", "rows")]
+HEADERS = ["pgvimp_device.cuh", "pgvimp_kernels.cuh", "pgvimp_cr.cuh", "pgvimp_plan.h", "pgvimp_launch.h",
+           "pgvimp_internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "-I", os.path.join(ROOT, "include")]
 
@@ -31,20 +33,37 @@ def _nvcc():
     return "nvcc"
 
 
-def _deps_mtime():
-    files = [os.path.join(CSRC, h) for h in HEADERS] + [os.path.join(ROOT, "include", "pgvimp.h")]
+def _headers_of(src: str):
+    """The headers a translation unit includes (directly or through another)."""
+    base = ["pgvimp_plan.h"]
+    if src.startswith("k"):
+        base += ["pgvimp_device.cuh", "pgvimp_kernels.cuh", "pgvimp_launch.h"]
+        if "_cta_" in src:
+            base += ["pgvimp_cr.cuh"]
+    elif src == "pgvimp_api.cu":
+        base += ["pgvimp_device.cuh", "pgvimp_launch.h", "pgvimp_internal.h"]
+    elif src == "pgvimp_server.cu":
+        base += ["pgvimp_internal.h"]
+    elif src == "pgvimp_noalloc.cu":
+        base += ["pgvimp_device.cuh"]
+    else:
+        base = list(HEADERS)
+    return base
+
+
+def _deps_mtime(src: str):
+    files = [os.path.join(CSRC, h) for h in _headers_of(src)] + [os.path.join(ROOT, "include", "pgvimp.h")]
     return max(os.path.getmtime(f) for f in files)
 
 
 def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) -> str:
     os.makedirs(os.path.join(OUT, "obj"), exist_ok=True)
     nvcc = _nvcc()
-    dep_t = _deps_mtime()
     jobs = []
     for src in SOURCES:
         s = os.path.join(CSRC, src)
         o = os.path.join(OUT, "obj", src.replace(".cu", ".o"))
-        if force or not os.path.exists(o) or os.path.getmtime(o) < max(os.path.getmtime(s), dep_t):
+        if force or not os.path.exists(o) or os.path.getmtime(o) < max(os.path.getmtime(s), _deps_mtime(src)):
             cmd = [nvcc, *ARCH, *NVCC_FLAGS, "-c", s, "-o", o]
             if ptxas_info:
                 cmd.insert(1, "-Xptxas=-v")

@@ -15,17 +15,25 @@
 #include "pgvimp_plan.h"
 
 #include "pgvimp_launch.h"
+#include "pgvimp_internal.h"
 
 namespace pgv {
 // Dispatch of a phase to the kernels of state dimension n and precision.
-static cudaError_t launch_phase(int n, const Launch& L, int phase, int arg_i, double arg_d, int precision) {
-  constexpr int ITER = 102;
+static cudaError_t launch_phase(int n, const Launch& L, int phase, int arg_i, double arg_d, int precision, int tpb) {
+  constexpr int PRIOR = 100, INIT = 101, ITER = 102, SLR = 103;
   const bool rows = (phase == PGVIMP_PHASE_MARGINALS || phase == PGVIMP_PHASE_QUAD || phase == PGVIMP_PHASE_TRIAL);
   const bool df = (precision == PGVIMP_PREC_MIXED_DF);
   const int qt32 = (precision != PGVIMP_PREC_PLAIN_FP64);
   switch (n) {
 #define PGV_CASE(N_)                                                                                      \
   case N_:                                                                                                \
+    if (tpb && !df) {                                                                                     \
+      if (phase == ITER)                                                                                  \
+        return qt32 ? launch_iter_cta<N_, float, double>(L, arg_i, tpb)                                   \
+                    : launch_iter_cta<N_, double, double>(L, arg_i, tpb);                                 \
+      if (phase == INIT || phase == SLR || (phase == PRIOR && arg_i == 1))                                \
+        return launch_aux_cta<N_>(L, phase, arg_i, qt32, tpb);                                            \
+    }                                                                                                     \
     if (phase == ITER) {                                                                                  \
       if (df) return launch_iter<N_, float, df64>(L, arg_i);                                              \
       return qt32 ? launch_iter<N_, float, double>(L, arg_i) : launch_iter<N_, double, double>(L, arg_i); \
@@ -232,6 +240,9 @@ pgvimp_status validate(const pgvimp_problem& p, const pgvimp_options& o, int idx
   if (o.max_bisect < 0 || o.max_bisect > 60) return E(PGVIMP_EINVAL, "max_bisect out of range");
   if (o.iters < 0 || o.iters > (1 << 20)) return E(PGVIMP_EINVAL, "iters out of range");
   if (o.init_kind == 1 && !(o.init_scale > 0.0)) return E(PGVIMP_EINVAL, "init_scale must be positive");
+  if (o.plan_threads > 1 && (o.plan_threads < 32 || o.plan_threads > kCrMaxThreads || (o.plan_threads & 31)))
+    return E(PGVIMP_EINVAL, "plan_threads must be 0, 1, or a multiple of 32 in 32..256");
+  if (o.plan_threads < 0) return E(PGVIMP_EINVAL, "plan_threads must be 0, 1, or a multiple of 32 in 32..256");
   return PGVIMP_OK;
 }
 
@@ -251,6 +262,7 @@ struct PlanLayout {
 
 struct BatchImpl {
   int count = 0, n = 0, precision = 0, dyn = 0;
+  int tpb = 0;   // threads per plan in the block form (0: one thread per plan)
   int iters_opt = 0, slr_opt = 0;
   std::vector<pgvimp_problem> probs;
   std::vector<pgvimp_options> opts;
@@ -262,13 +274,14 @@ struct BatchImpl {
   bool owns_arena = false;
   char* h_in = nullptr;   // pinned INPUT staging
   char* h_out = nullptr;  // pinned OUTPUT staging (result + extra)
+  bool owns_host = true;  // false: the staging belongs to the caller (a server's pinned pool)
   bool started = false;
   int j_host = 0, kin_host = 0;
   std::string err;
   ~BatchImpl() {
     if (owns_arena && arena) cudaFree(arena);
-    if (h_in) cudaFreeHost(h_in);
-    if (h_out) cudaFreeHost(h_out);
+    if (owns_host && h_in) cudaFreeHost(h_in);
+    if (owns_host && h_out) cudaFreeHost(h_out);
   }
   char* d_in() const { return arena; }
   char* d_res() const { return arena + in_bytes; }
@@ -365,7 +378,11 @@ void plan_layout(BatchImpl& B) {
     L.Altv = take(work, 8 * (slr ? N * nn : 1));
     L.altv = take(work, 8 * (slr ? N * n : 1));
     L.xbar = take(work, 8 * (slr ? (N + 1) * n : 1));
-    L.scr = take(work, 8 * (N + 1) * (3 * nn + n));
+    // per-state scratch: the sequential sweeps need 3n^2 + n, the cyclic
+    // reduction of the block form 2 npe + 6 n^2 + 2 n (npe: packed, even)
+    const size_t np = n * (n + 1) / 2, npe = np + (np & 1);
+    const size_t scr_state = B.tpb ? std::max(3 * nn + n, 2 * npe + 6 * nn + 2 * n) : 3 * nn + n;
+    L.scr = take(work, 8 * (N + 1) * scr_state);
   }
   B.in_bytes = align256(in);
   B.res_bytes = align256(res);
@@ -485,7 +502,7 @@ pgvimp_status cuda_fail(std::string* err, cudaError_t e, const char* what) {
 
 pgvimp_status launch(BatchImpl& B, int phase, int arg_i, double arg_d, cudaStream_t s) {
   Launch L{reinterpret_cast<const PlanDesc*>(B.d_in() + B.off_desc), B.count, s};
-  cudaError_t e = launch_phase(B.n, L, phase, arg_i, arg_d, B.precision);
+  cudaError_t e = launch_phase(B.n, L, phase, arg_i, arg_d, B.precision, B.tpb);
   if (e != cudaSuccess) return cuda_fail(&B.err, e, "kernel launch");
   return PGVIMP_OK;
 }
@@ -535,6 +552,9 @@ static pgvimp_status prepare(int count, const pgvimp_problem* problems, const pg
     if (st != PGVIMP_OK) return st;
     if (problems[i].n != problems[0].n) return fail(&B.err, PGVIMP_EINVAL, "a batch needs one state dimension");
     if (problems[i].dyn_kind != problems[0].dyn_kind) return fail(&B.err, PGVIMP_EINVAL, "a batch needs one dynamics kind");
+    if ((options[i].plan_threads > 1) != (options[0].plan_threads > 1) ||
+        (options[i].plan_threads > 1 && options[i].plan_threads != options[0].plan_threads))
+      return fail(&B.err, PGVIMP_EINVAL, "a batch needs one plan_threads");
     if (problems[i].dyn_kind != PGVIMP_DYN_LINEAR &&
         (options[i].iters != options[0].iters || options[i].slr_iters != options[0].slr_iters))
       return fail(&B.err, PGVIMP_EINVAL, "an SLR batch needs one iters / slr_iters");
@@ -543,6 +563,9 @@ static pgvimp_status prepare(int count, const pgvimp_problem* problems, const pg
   B.n = problems[0].n;
   B.dyn = problems[0].dyn_kind;
   B.precision = precision;
+  B.tpb = options[0].plan_threads > 1 ? options[0].plan_threads : 0;
+  if (B.tpb && precision == PGVIMP_PREC_MIXED_DF)
+    return fail(&B.err, PGVIMP_EINVAL, "the block form (plan_threads > 1) runs FP64 or mixed recursions only");
   B.iters_opt = options[0].iters;
   B.slr_opt = options[0].slr_iters;
   B.probs.assign(problems, problems + count);
@@ -561,8 +584,9 @@ pgvimp_status pgvimp_batch_arena_bytes(int count, const pgvimp_problem* problems
   return PGVIMP_OK;
 }
 
-pgvimp_status pgvimp_batch_create(int count, const pgvimp_problem* problems, const pgvimp_options* options,
-                                  int precision, void* arena, size_t arena_bytes, pgvimp_batch** out) {
+static pgvimp_status create_batch(int count, const pgvimp_problem* problems, const pgvimp_options* options,
+                                  int precision, void* arena, size_t arena_bytes, void* h_in, void* h_out,
+                                  pgvimp_batch** out) {
   if (!out) return fail(nullptr, PGVIMP_EINVAL, "out is NULL");
   *out = nullptr;
   pgvimp_batch* B = new (std::nothrow) pgvimp_batch();
@@ -592,8 +616,12 @@ pgvimp_status pgvimp_batch_create(int count, const pgvimp_problem* problems, con
     }
     B->owns_arena = true;
   }
-  if (cudaMallocHost(&B->h_in, B->in_bytes) != cudaSuccess ||
-      cudaMallocHost(&B->h_out, B->res_bytes + B->extra_bytes) != cudaSuccess) {
+  if (h_in && h_out) {
+    B->h_in = static_cast<char*>(h_in);
+    B->h_out = static_cast<char*>(h_out);
+    B->owns_host = false;
+  } else if (cudaMallocHost(&B->h_in, B->in_bytes) != cudaSuccess ||
+             cudaMallocHost(&B->h_out, B->res_bytes + B->extra_bytes) != cudaSuccess) {
     delete B;
     return fail(nullptr, PGVIMP_ENOMEM, "pinned host staging allocation failed");
   }
@@ -608,6 +636,11 @@ pgvimp_status pgvimp_batch_create(int count, const pgvimp_problem* problems, con
   }
   *out = B;
   return PGVIMP_OK;
+}
+
+pgvimp_status pgvimp_batch_create(int count, const pgvimp_problem* problems, const pgvimp_options* options,
+                                  int precision, void* arena, size_t arena_bytes, pgvimp_batch** out) {
+  return create_batch(count, problems, options, precision, arena, arena_bytes, nullptr, nullptr, out);
 }
 
 pgvimp_status pgvimp_batch_upload(pgvimp_batch* b, void* stream) {
@@ -917,6 +950,31 @@ pgvimp_status pgvimp_destroy(pgvimp_ctx* c) {
 }
 
 }  // extern "C"
+
+// ---- internal entry points for the server (pgvimp_internal.h)
+pgvimp_status pgv::batch_sizes(int count, const pgvimp_problem* problems, const pgvimp_options* options,
+                               int precision, BatchSizes* sz) {
+  BatchImpl B;
+  pgvimp_status st = prepare(count, problems, options, precision, B);
+  if (st != PGVIMP_OK) return st;
+  sz->dev = B.total();
+  sz->host_in = B.in_bytes;
+  sz->host_out = B.res_bytes + B.extra_bytes;
+  return PGVIMP_OK;
+}
+
+pgvimp_status pgv::batch_create_staged(int count, const pgvimp_problem* problems, const pgvimp_options* options,
+                                       int precision, void* arena, size_t arena_bytes, void* h_in, void* h_out,
+                                       pgvimp_batch** out) {
+  if (!arena || !h_in || !h_out) return fail(nullptr, PGVIMP_EINVAL, "staged batch needs arena and staging");
+  return create_batch(count, problems, options, precision, arena, arena_bytes, h_in, h_out, out);
+}
+
+int pgv::batch_plan_status(const pgvimp_batch* b, int index) {
+  const double* sc = reinterpret_cast<const double*>(b->h_out + b->off_scal) + (size_t)kScal * index;
+  return (int)sc[S_STATUS];
+}
+
 
 static pgvimp_status finalize(pgvimp_batch* b, cudaStream_t s) {
   // The iterate may sit in buffer set 1 or 2; results are read from set 0

@@ -16,6 +16,7 @@ constexpr int kMaxDof = 8;       // largest arm chain
 constexpr int kMaxSpheres = 64;
 constexpr int kMaxGH = 10;       // largest points-per-dimension of the GH rule
 constexpr int kScal = 24;        // per-plan scalar slots
+constexpr int kCrMaxThreads = 256; // largest thread block of the block (latency) form
 
 // Per-plan scalar slots (doubles).
 enum ScalSlot {

@@ -18,6 +18,23 @@ TOL_FP64_SMALL = dict(mu=1e-9, sigma=1e-9)
 TOL_FP64_DENSE = dict(mu=2e-6, sigma=2e-6)
 
 
+def fp64_tol_from_conditioning(pb, floor=1e-9):
+    """FP64 bound for two elimination orders of the same chain: 10 kappa u,
+    with kappa the 2-norm condition number of the prior precision K^-1 (the
+    initial Lambda) and u = 2^-53; never below `floor`.  For the C1 robot
+    kappa is 9e5 at N = 50, 1.5e7 at N = 100 and 4.7e10 at N = 750."""
+    pr = oracle.prior(pb)
+    n, N = pb.n, pb.N
+    D = n * (N + 1)
+    M = np.zeros((D, D))
+    for i in range(N + 1):
+        M[i * n:(i + 1) * n, i * n:(i + 1) * n] = pr.Kd[i]
+    for i in range(N):
+        M[(i + 1) * n:(i + 2) * n, i * n:(i + 1) * n] = pr.Ko[i]
+        M[i * n:(i + 1) * n, (i + 1) * n:(i + 2) * n] = pr.Ko[i].T
+    return max(floor, 10.0 * np.linalg.cond(M) * 2.0 ** -53)
+
+
 def rel_mu(a, b):
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 

@@ -110,3 +110,21 @@ def test_plans_sharing_a_map_store_it_once(pg):
     shared = arena([pb, replace(pb, muN=pb.muN + 0.1)])
     separate = arena([pb, replace(pb, sdf=np.array(pb.sdf, copy=True))])
     assert separate - shared >= grid
+
+
+def test_plan_threads_validation(pg):
+    """The block form takes 32..256 threads in multiples of 32, one value per batch."""
+    from paper_2411_03416_b300 import _lib
+    pb, op = W.c1_point2d()
+    for bad in (-1, 2, 48, 288, 512):
+        assert _arena_status(pg, pb, replace(op, plan_threads=bad))[0] == _lib.EINVAL
+    for good in (0, 1, 32, 64, 256):
+        assert _arena_status(pg, pb, replace(op, plan_threads=good))[0] == 0
+    keep = _lib._Keep()
+    parr = (_lib.Problem * 2)(*[_lib.marshal_problem(pb, keep) for _ in range(2)])
+    oarr = (_lib.Options * 2)(_lib.marshal_options(op), _lib.marshal_options(replace(op, plan_threads=64)))
+    nb = C.c_size_t(0)
+    st = pg.lib().pgvimp_batch_arena_bytes(2, C.cast(parr, C.c_void_p), C.cast(oarr, C.c_void_p), 1, C.byref(nb))
+    assert st == _lib.EINVAL
+    # the block form runs FP64 or mixed recursions, not double-float
+    assert _arena_status(pg, pb, replace(op, plan_threads=64), precision=2)[0] == _lib.EINVAL

@@ -1,0 +1,100 @@
+"""The block (latency) form: one thread block per plan, block recursions by
+cyclic reduction over time.  The same plans as the thread form, against the
+oracle, at the sizes and edge cases where the reduction's level structure
+changes (N a power of two, one more or one less, N = 1)."""
+from dataclasses import replace
+
+import numpy as np
+import pytest
+
+import workloads as W
+from _parity import TOL_FP64_SMALL, TOL_MIXED, compare_plan, fp64_tol_from_conditioning, gpu_solve
+
+pytestmark = pytest.mark.gpu
+
+MIXED, FP64, MIXED_DF = 1, 0, 2
+
+
+@pytest.fixture(scope="module")
+def pg():
+    import torch
+    assert torch.cuda.is_available(), "these tests need a CUDA device"
+    import paper_2411_03416_b300 as pg
+    pg.lib()
+    return pg
+
+
+def block(op, tpb=64):
+    return replace(op, plan_threads=tpb)
+
+
+@pytest.mark.parametrize("prec,tol", [(FP64, TOL_FP64_SMALL), (MIXED, TOL_MIXED)])
+def test_c1_point2d_block_form(pg, prec, tol):
+    pb, op = W.c1_point2d()
+    res = gpu_solve([pb], [block(op)], prec)[0]
+    compare_plan(pb, op, res, rtol_mu=tol["mu"], rtol_sigma=tol["sigma"])
+    assert len(res.logs) == op.iters
+
+
+@pytest.mark.parametrize("N", [1, 2, 3, 7, 8, 9, 31, 32, 33, 64, 100])
+@pytest.mark.parametrize("tpb", [32, 128])
+def test_reduction_levels_fp64(pg, N, tpb):
+    """Every level structure of the cyclic reduction, including states with
+    only a left neighbour, more threads than states and the reverse."""
+    pb, op = W.c1_point2d(N=N, iters=4)
+    op = replace(op, kl_eps=0.05 * (N + 1))       # binds: the bisection runs several trials
+    res = gpu_solve([pb], [block(op, tpb)], FP64)[0]
+    tol = fp64_tol_from_conditioning(pb)
+    compare_plan(pb, op, res, rtol_mu=tol, rtol_sigma=tol)
+
+
+@pytest.mark.parametrize("prec,tol", [(FP64, TOL_FP64_SMALL), (MIXED, TOL_MIXED)])
+def test_c3_arm_block_form(pg, prec, tol):
+    pb, op = W.c3_arm(N=30, iters=10)
+    res = gpu_solve([pb], [block(op, 32)], prec)[0]
+    compare_plan(pb, op, res, rtol_mu=tol["mu"], rtol_sigma=tol["sigma"])
+
+
+def test_c4_quadrotor_slr_block_form_fp64(pg):
+    """Alg. 2 with the SLR linearisation and the LTV prior spread over the block."""
+    pb, op = W.c4_quadrotor(N=40, iters=5, slr_iters=3)
+    res = gpu_solve([pb], [block(op)], FP64)[0]
+    compare_plan(pb, op, res, rtol_mu=3e-8, rtol_sigma=1e-6)
+    assert len(res.logs) == 15
+
+
+@pytest.mark.parametrize("N", [40, 300])
+def test_c4_quadrotor_first_linearisation_block_form_mixed(pg, N):
+    pb, op = W.c4_quadrotor(N=N, iters=2, slr_iters=1)
+    res = gpu_solve([pb], [block(op, 128)], MIXED)[0]
+    compare_plan(pb, op, res, rtol_mu=TOL_MIXED["mu"], rtol_sigma=TOL_MIXED["sigma"])
+
+
+@pytest.mark.parametrize("iters", [1, 2])
+@pytest.mark.parametrize("prec,tol", [(FP64, dict(mu=1e-5, sigma=1e-5)), (MIXED, TOL_MIXED)])
+def test_c2_dense_horizon_block_form_first_iterations(pg, prec, tol, iters):
+    pb, op = W.c2_point2d_dense(iters=iters)
+    res = gpu_solve([pb], [block(op, 128)], prec)[0]
+    compare_plan(pb, op, res, rtol_mu=tol["mu"], rtol_sigma=tol["sigma"])
+
+
+def test_block_form_matches_thread_form(pg):
+    """Two elimination orders of the same SPD chains: FP64 results agree to
+    rounding on a non-chaotic plan, with the same step sizes."""
+    pb, op = W.c1_point2d(N=60, iters=12)
+    a = gpu_solve([pb], [op], FP64)[0]
+    b = gpu_solve([pb], [block(op, 64)], FP64)[0]
+    assert [l["beta"] for l in a.logs] == [l["beta"] for l in b.logs]
+    assert np.linalg.norm(a.mu - b.mu) <= 1e-10 * np.linalg.norm(a.mu)
+    assert np.max(np.abs(a.Sd - b.Sd)) <= 1e-10 * np.max(np.abs(a.Sd))
+
+
+@pytest.mark.parametrize("prec", [MIXED, FP64])
+def test_block_form_batch_equals_alone(pg, prec):
+    probs = [W.c1_point2d(request=r, N=N, iters=6) for r, N in enumerate([7, 50, 33, 1, 64])]
+    pbs, ops = [p for p, _ in probs], [block(o) for _, o in probs]
+    together = gpu_solve(pbs, ops, prec)
+    for i in range(len(pbs)):
+        alone = gpu_solve([pbs[i]], [ops[i]], prec)[0]
+        np.testing.assert_array_equal(together[i].mu, alone.mu)
+        np.testing.assert_array_equal(together[i].Sd, alone.Sd)

@@ -77,6 +77,7 @@ class Options:
     init_kind: int = 0
     init_scale: float = 1.0
     replay_beta: Optional[np.ndarray] = None
+    plan_threads: int = 0   # execution form of the CUDA path (0: thread per plan; 32..256: block per plan)
 
 
 def rng_for(config: int, request: int = 0) -> np.random.Generator:
