@@ -27,6 +27,9 @@ import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
+# The server overlaps batches on up to 16 streams; with CUDA's default of 8
+# hardware work queues, streams share queues and their kernels serialise.
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
 
 METRIC = "plans/sec and p50/p99 plan latency, served FP32/FP64 vs plain FP64, 1 B300"
 ITERS, N_STEPS, GH_P = 30, 750, 5
@@ -256,7 +259,7 @@ def _pct(v, q):
     return float(np.percentile(np.asarray(v, dtype=float), q)) if len(v) else None
 
 
-def run_served(mix, precision, plan_threads, max_inflight=16, max_batch=32, window_ms=2.0):
+def run_served(mix, precision, plan_threads, max_inflight=16, max_batch=32, window_ms=2.0, submitters=4):
     """Replays the mix's arrival times against a server (continuous batching)
     and returns plans/s (count / time from the first arrival to the last
     result on the host) and p50/p99 latency (arrival to result on the host)."""
@@ -271,21 +274,23 @@ def run_served(mix, precision, plan_threads, max_inflight=16, max_batch=32, wind
         if key not in seen:
             seen.add(key)
             srv.poll(srv.submit(rq.problem, rq.options))
+    ready = [srv.prepare(rq.problem, rq.options) for rq in mix]
     ids = [None] * len(mix)
     lags = []
     t0 = time.perf_counter()
     s0 = srv.stats()["now_ms"]
 
-    def submitter():
-        for k, rq in enumerate(mix):
-            d = t0 + rq.arrival_s - time.perf_counter()
+    def submitter(first):
+        for k in range(first, len(mix), submitters):
+            d = t0 + mix[k].arrival_s - time.perf_counter()
             if d > 0:
                 time.sleep(d)
-            ids[k] = srv.submit(rq.problem, rq.options)
-            lags.append(time.perf_counter() - t0 - rq.arrival_s)
+            ids[k] = srv.submit(ready[k])
+            lags.append(time.perf_counter() - t0 - mix[k].arrival_s)
 
-    th = threading.Thread(target=submitter)
-    th.start()
+    ths = [threading.Thread(target=submitter, args=(j,)) for j in range(submitters)]
+    for th in ths:
+        th.start()
     lat, done, sizes = [], [], []
     for k, rq in enumerate(mix):
         while ids[k] is None:
@@ -294,23 +299,24 @@ def run_served(mix, precision, plan_threads, max_inflight=16, max_batch=32, wind
         lat.append(info["done_ms"] - (s0 + 1000.0 * rq.arrival_s))
         done.append(info["done_ms"] - s0)
         sizes.append(info["batch_size"])
-    th.join()
+    for th in ths:
+        th.join()
     st = srv.stats()
     srv.close()
     span_s = max(done) / 1000.0
     return {"plans_per_s": len(mix) / span_s, "p50_ms": _pct(lat, 50), "p99_ms": _pct(lat, 99),
             "makespan_s": span_s, "requests": len(mix), "batches": st["batches"] - len(seen),
             "mean_batch": sum(sizes) / len(sizes), "submit_lag_ms_max": 1000.0 * max(lags),
+            "host_launch_ms": st["host_launch_ms"], "host_collect_ms": st["host_collect_ms"],
             "precision": precision, "plan_threads": plan_threads, "max_inflight": max_inflight,
             "max_batch": max_batch, "batch_window_ms": window_ms}
 
 
-def run_plain(mix, plan_threads):
+def run_plain(mix):
     """Plain per-request FP64: one plan at a time through the single-plan calls
     (pgvimp_create / plan / get / destroy) on one stream, no batching, in
-    arrival order; latency from arrival to the result on the host."""
-    from dataclasses import replace
-
+    arrival order; latency from arrival to the result on the host.  Each
+    request keeps its options' execution form."""
     import paper_2411_03416_b300 as pg
     from paper_2411_03416_b300 import _lib as L
     seen = set()
@@ -318,7 +324,7 @@ def run_plain(mix, plan_threads):
         key = (rq.problem.n, rq.problem.dyn_kind)
         if key not in seen:
             seen.add(key)
-            c = pg.Context(rq.problem, replace(rq.options, plan_threads=plan_threads), L.PREC_PLAIN_FP64)
+            c = pg.Context(rq.problem, rq.options, L.PREC_PLAIN_FP64)
             c.plan()
             c.get()
             c.close()
@@ -328,30 +334,43 @@ def run_plain(mix, plan_threads):
         d = t0 + rq.arrival_s - time.perf_counter()
         if d > 0:
             time.sleep(d)
-        c = pg.Context(rq.problem, replace(rq.options, plan_threads=plan_threads), L.PREC_PLAIN_FP64)
+        c = pg.Context(rq.problem, rq.options, L.PREC_PLAIN_FP64)
         c.plan()
         c.get()
         c.close()
         lat.append(1000.0 * (time.perf_counter() - t0 - rq.arrival_s))
     span_s = time.perf_counter() - t0
     return {"plans_per_s": len(mix) / span_s, "p50_ms": _pct(lat, 50), "p99_ms": _pct(lat, 99),
-            "makespan_s": span_s, "requests": len(mix), "precision": 0, "plan_threads": plan_threads}
+            "makespan_s": span_s, "requests": len(mix), "precision": 0}
 
 
 def serving(args):
+    from dataclasses import replace
+
     import workloads as W
+    from paper_2411_03416_b300 import autotune
     mix = W.c5_mix(args.serve_count)
+    # block size per (n, dynamics, horizon bucket), tuned on one request of each bucket
+    tuner = autotune.Tuner()
+    reps = {}
+    for rq in mix:
+        reps.setdefault(autotune.bucket(rq.problem), (rq.problem, rq.options))
+    t = time.perf_counter()
+    tuner.tune(reps.values(), precision=1, repeats=1, copies=148)   # one plan per SM: a loaded GPU
+    tune_s = time.perf_counter() - t
+    mix = [replace(rq, options=tuner.apply(rq.problem, rq.options)) for rq in mix]
     out = {"workload": f"serving mix: {args.serve_count} requests, Poisson arrivals at 2000/s; 50% 2-D point robot "
                        "N~U{50..1000}, 30% planar quadrotor SLR N~U{100..500}, 20% 7-DOF arm N~U{100..300}; "
                        "own seeded map per request; 80 GB admission budget",
            "latency": "arrival to result on the host (server clock)"}
     # served FP32/FP64: FP32 quadrature, FP64 recursions, block form, continuous batching
-    out["served_fp32_fp64"] = run_served(mix, 1, args.serve_threads)
-    out["served_plain_fp64"] = run_served(mix, 0, args.serve_threads)
+    out["autotune"] = {"seconds": tune_s, "table": {f"n{k[0]}/dyn{k[1]}/log2N{k[2]}": v for k, v in tuner.table.items()}}
+    out["served_fp32_fp64"] = run_served(mix, 1, -1)
+    out["served_plain_fp64"] = run_served(mix, 0, -1)
     sample = mix[:args.plain_count]
     out["plain_sample"] = f"first {len(sample)} requests of the mix (arrival times kept)"
-    out["plain_fp64_per_request"] = run_plain(sample, args.serve_threads)
-    out["served_fp32_fp64_on_sample"] = run_served(sample, 1, args.serve_threads)
+    out["plain_fp64_per_request"] = run_plain(sample)
+    out["served_fp32_fp64_on_sample"] = run_served(sample, 1, -1)
     return out
 
 
@@ -368,7 +387,7 @@ def kernel_only(args):
 
     from paper_2411_03416_b300 import _lib as L
     probs, opts = make_batch_problems(args.batch)
-    opts = [replace(o, iters=args.iters) for o in opts]
+    opts = [replace(o, iters=args.iters, plan_threads=args.plan_threads) for o in opts]
     b = L.Batch(probs, opts, PRECISIONS[args.precision])
     st = torch.cuda.Stream()
     sh = st.cuda_stream
@@ -386,7 +405,8 @@ def kernel_only(args):
     trials = [sum(l["trials"] for l in b.result(i, full=False).logs) for i in range(args.batch)]
     ms = e0.elapsed_time(e1)
     flops = algorithmic_fp64_flops(probs, trials, args.iters)
-    print(f"kernel-only: batch {args.batch}, {args.iters} iterations, {args.precision}: {ms:.1f} ms, "
+    print(f"kernel-only: batch {args.batch}, {args.iters} iterations, {args.precision}, "
+          f"plan_threads {args.plan_threads}: {ms:.1f} ms, "
           f"{sum(trials)} trials, {flops / ms / 1e9:.4f} TFLOP/s-equivalent", flush=True)
     b.close()
 
@@ -408,9 +428,10 @@ def main():
     ap.add_argument("--kernel-only", action="store_true",
                     help="profiling target: prior phase, then one fused-iteration launch; no JSON line")
     ap.add_argument("--iters", type=int, default=ITERS, help="proximal iterations (kernel-only mode)")
+    ap.add_argument("--plan-threads", type=int, default=0,
+                    help="kernel-only mode: 0 thread form, 32..256 block form (threads per plan)")
     ap.add_argument("--serve-count", type=int, default=512, help="requests of the serving mix (0: skip serving)")
     ap.add_argument("--plain-count", type=int, default=32, help="requests of the plain per-request FP64 sample")
-    ap.add_argument("--serve-threads", type=int, default=64, help="threads per plan in the served block form")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -245,7 +245,8 @@ typedef struct {
   size_t hbm_budget_bytes;   /* device pool for admitted batches (>= 1 MiB) */
   size_t host_staging_bytes; /* pinned host pool (0: min(hbm_budget_bytes, 4 GiB)) */
   int precision;             /* pgvimp_precision of every served plan */
-  int plan_threads;          /* execution form of every served plan (pgvimp_options.plan_threads) */
+  int plan_threads;          /* execution form of every served plan (pgvimp_options.plan_threads), or -1:
+                                each request's own options.plan_threads (e.g. from an autotuner) */
   int max_inflight;          /* batches on the device at once, 1..64 */
   int max_batch;             /* plans per batch, >= 1 */
   double batch_window_ms;    /* longest wait of a queued request for batch company, >= 0 */
@@ -262,13 +263,16 @@ typedef struct {
   uint64_t batches, plans;   /* launched so far */
   size_t dev_used, host_used;
   double now_ms;             /* server clock */
+  double host_launch_ms;     /* scheduler time spent creating and queueing batches */
+  double host_collect_ms;    /* scheduler time spent copying results out */
 } pgvimp_server_stats_t;
 
 /* Creates the pools, streams and the scheduler thread on the current device.
  * EINVAL for a bad config, ENOMEM if a pool cannot be allocated. */
 pgvimp_status pgvimp_server_create(const pgvimp_server_config *cfg, pgvimp_server **out);
 /* Validates and deep-copies one request (the caller may free its arrays on
- * return) and queues it.  options.plan_threads is replaced by the server's.
+ * return) and queues it.  options.plan_threads is replaced by the server's
+ * unless the server was created with plan_threads = -1.
  * ENOMEM if the request alone exceeds a pool; validation as pgvimp_batch_create. */
 pgvimp_status pgvimp_submit(pgvimp_server *s, const pgvimp_problem *problem, const pgvimp_options *options,
                             uint64_t *request_id);

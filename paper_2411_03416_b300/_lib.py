@@ -93,6 +93,7 @@ class ServerStats(C.Structure):
     _fields_ = [
         ("queued", C.c_int), ("inflight", C.c_int), ("batches", C.c_uint64), ("plans", C.c_uint64),
         ("dev_used", C.c_size_t), ("host_used", C.c_size_t), ("now_ms", C.c_double),
+        ("host_launch_ms", C.c_double), ("host_collect_ms", C.c_double),
     ]
 
 
@@ -385,13 +386,18 @@ class Server:
         self.h = h
         self._sizes = {}
 
-    def submit(self, problem, options) -> int:
+    @staticmethod
+    def prepare(problem, options):
+        """Marshals a request once (so that a timed submit only crosses the C ABI)."""
         keep = _Keep()
-        p = marshal_problem(problem, keep)
-        o = marshal_options(options)
+        return (marshal_problem(problem, keep), marshal_options(options), keep, (problem.n, problem.N))
+
+    def submit(self, problem, options=None) -> int:
+        """Queues a request: (problem, options), or a tuple from prepare()."""
+        p, o, keep, size = problem if options is None else self.prepare(problem, options)
         rid = C.c_uint64(0)
         _check(lib().pgvimp_submit(self.h, C.byref(p), C.byref(o), C.byref(rid)))
-        self._sizes[rid.value] = (problem.n, problem.N)
+        self._sizes[rid.value] = size
         return rid.value
 
     def poll(self, rid: int, timeout_ms: int = -1):

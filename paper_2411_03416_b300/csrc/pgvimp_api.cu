@@ -178,7 +178,10 @@ int cost_dims(const pgvimp_problem& p) {
   }
 }
 
-pgvimp_status validate(const pgvimp_problem& p, const pgvimp_options& o, int idx, std::string* err) {
+// `scan_grid` = false skips the per-cell finiteness scan of the SDF (for
+// requests a server already validated at submit).
+pgvimp_status validate(const pgvimp_problem& p, const pgvimp_options& o, int idx, std::string* err,
+                       bool scan_grid = true) {
   auto E = [&](pgvimp_status st, const std::string& m) { return fail(err, st, "problem " + std::to_string(idx) + ": " + m); };
   if (!supported_n(p.n)) return E(PGVIMP_EINVAL, "state dimension n must be one of 4, 6, 14");
   if (p.m < 1 || p.m > kMaxN) return E(PGVIMP_EINVAL, "noise dimension m out of range");
@@ -216,7 +219,7 @@ pgvimp_status validate(const pgvimp_problem& p, const pgvimp_options& o, int idx
     if (three && p.sdf_nz < 2) return E(PGVIMP_EINVAL, "3-D cost needs sdf_nz >= 2");
     if (!(p.sdf_cell > 0.0) || !finite_all(p.sdf_origin, 3)) return E(PGVIMP_EINVAL, "bad SDF geometry");
     size_t cells = (size_t)p.sdf_nx * p.sdf_ny * (three ? p.sdf_nz : 1);
-    for (size_t i = 0; i < cells; ++i)
+    for (size_t i = 0; scan_grid && i < cells; ++i)
       if (!std::isfinite(p.sdf[i])) return E(PGVIMP_ENOTFINITE, "SDF not finite");
   }
   if (p.cost_kind == PGVIMP_COST_ARM) {
@@ -543,12 +546,12 @@ const char* pgvimp_last_error(const void* ctx) {
 }
 
 static pgvimp_status prepare(int count, const pgvimp_problem* problems, const pgvimp_options* options, int precision,
-                             BatchImpl& B) {
+                             BatchImpl& B, bool scan_grids = true) {
   if (count < 1 || !problems || !options) return fail(&B.err, PGVIMP_EINVAL, "count must be >= 1 with problems and options");
   if (precision != PGVIMP_PREC_PLAIN_FP64 && precision != PGVIMP_PREC_MIXED && precision != PGVIMP_PREC_MIXED_DF)
     return fail(&B.err, PGVIMP_EINVAL, "unknown precision");
   for (int i = 0; i < count; ++i) {
-    pgvimp_status st = validate(problems[i], options[i], i, &B.err);
+    pgvimp_status st = validate(problems[i], options[i], i, &B.err, scan_grids);
     if (st != PGVIMP_OK) return st;
     if (problems[i].n != problems[0].n) return fail(&B.err, PGVIMP_EINVAL, "a batch needs one state dimension");
     if (problems[i].dyn_kind != problems[0].dyn_kind) return fail(&B.err, PGVIMP_EINVAL, "a batch needs one dynamics kind");
@@ -586,12 +589,12 @@ pgvimp_status pgvimp_batch_arena_bytes(int count, const pgvimp_problem* problems
 
 static pgvimp_status create_batch(int count, const pgvimp_problem* problems, const pgvimp_options* options,
                                   int precision, void* arena, size_t arena_bytes, void* h_in, void* h_out,
-                                  pgvimp_batch** out) {
+                                  pgvimp_batch** out, bool scan_grids = true) {
   if (!out) return fail(nullptr, PGVIMP_EINVAL, "out is NULL");
   *out = nullptr;
   pgvimp_batch* B = new (std::nothrow) pgvimp_batch();
   if (!B) return fail(nullptr, PGVIMP_ENOMEM, "host allocation failed");
-  pgvimp_status st = prepare(count, problems, options, precision, *B);
+  pgvimp_status st = prepare(count, problems, options, precision, *B, scan_grids);
   ensure_tables();
   if (st != PGVIMP_OK) {
     delete B;
@@ -953,9 +956,9 @@ pgvimp_status pgvimp_destroy(pgvimp_ctx* c) {
 
 // ---- internal entry points for the server (pgvimp_internal.h)
 pgvimp_status pgv::batch_sizes(int count, const pgvimp_problem* problems, const pgvimp_options* options,
-                               int precision, BatchSizes* sz) {
+                               int precision, BatchSizes* sz, bool scan_grids) {
   BatchImpl B;
-  pgvimp_status st = prepare(count, problems, options, precision, B);
+  pgvimp_status st = prepare(count, problems, options, precision, B, scan_grids);
   if (st != PGVIMP_OK) return st;
   sz->dev = B.total();
   sz->host_in = B.in_bytes;
@@ -965,9 +968,9 @@ pgvimp_status pgv::batch_sizes(int count, const pgvimp_problem* problems, const 
 
 pgvimp_status pgv::batch_create_staged(int count, const pgvimp_problem* problems, const pgvimp_options* options,
                                        int precision, void* arena, size_t arena_bytes, void* h_in, void* h_out,
-                                       pgvimp_batch** out) {
+                                       pgvimp_batch** out, bool scan_grids) {
   if (!arena || !h_in || !h_out) return fail(nullptr, PGVIMP_EINVAL, "staged batch needs arena and staging");
-  return create_batch(count, problems, options, precision, arena, arena_bytes, h_in, h_out, out);
+  return create_batch(count, problems, options, precision, arena, arena_bytes, h_in, h_out, out, scan_grids);
 }
 
 int pgv::batch_plan_status(const pgvimp_batch* b, int index) {

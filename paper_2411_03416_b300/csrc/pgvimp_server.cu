@@ -2,9 +2,9 @@
 //
 // Requests (problem + options) arrive from any host thread.  A scheduler
 // thread packs queued requests of a compatible kind (state dimension,
-// dynamics kind, and for SLR plans the iteration counts) into a batch as soon
-// as a launch slot, device memory and pinned staging are free, and launches
-// the whole plan (upload, prior, iterations, result download) on one of
+// dynamics kind, execution form, and for SLR plans the iteration counts) into
+// a batch as soon as a launch slot, device memory and pinned staging are
+// free, and launches the whole plan (upload, prior, iterations, result download) on one of
 // several streams, so that batches admitted while others run overlap on the
 // GPU.  A stream callback hands the finished batch back to the scheduler,
 // which copies each plan's result out, frees the batch's memory and admits
@@ -123,8 +123,10 @@ struct OwnedProblem {
 
 // Requests that may share a batch.
 struct GroupKey {
-  int n, dyn, iters, slr;
-  bool operator==(const GroupKey& o) const { return n == o.n && dyn == o.dyn && iters == o.iters && slr == o.slr; }
+  int n, dyn, iters, slr, tpb;
+  bool operator==(const GroupKey& o) const {
+    return n == o.n && dyn == o.dyn && iters == o.iters && slr == o.slr && tpb == o.tpb;
+  }
 };
 
 struct Request {
@@ -165,6 +167,7 @@ struct pgvimp_server {
   bool stop = false;
   uint64_t next_id = 1;
   uint64_t launched_batches = 0, launched_plans = 0;
+  double host_launch_ms = 0.0, host_collect_ms = 0.0;   // scheduler time spent preparing / collecting batches
   std::thread worker;
   std::chrono::steady_clock::time_point t0;
 
@@ -206,13 +209,11 @@ pgvimp_status launch_flight(pgvimp_server* S, Flight* f) {
   std::vector<pgvimp_options> opts;
   for (Request* r : f->reqs) {
     probs.push_back(r->prob.p);
-    pgvimp_options o = r->opt;
-    o.plan_threads = S->cfg.plan_threads;
-    opts.push_back(o);
+    opts.push_back(r->opt);
   }
   pgvimp_status st = batch_create_staged((int)probs.size(), probs.data(), opts.data(), S->cfg.precision,
                                          S->dev_pool + f->dev_off, f->dev_bytes, S->host_pool + f->hin_off,
-                                         S->host_pool + f->hout_off, &f->b);
+                                         S->host_pool + f->hout_off, &f->b, false);
   if (st != PGVIMP_OK) return st;
   void* s = S->streams[f->slot];
   if ((st = pgvimp_batch_upload(f->b, s)) || (st = pgvimp_batch_reset(f->b, s)) || (st = pgvimp_batch_run(f->b, 0, s)) ||
@@ -286,12 +287,10 @@ Flight* form_flight(pgvimp_server* S) {
     std::vector<pgvimp_options> opts;
     for (size_t i = 0; i < cnt; ++i) {
       probs.push_back(cand[i]->prob.p);
-      pgvimp_options o = cand[i]->opt;
-      o.plan_threads = S->cfg.plan_threads;
-      opts.push_back(o);
+      opts.push_back(cand[i]->opt);
     }
     BatchSizes sz;
-    if (batch_sizes((int)cnt, probs.data(), opts.data(), S->cfg.precision, &sz) != PGVIMP_OK) {
+    if (batch_sizes((int)cnt, probs.data(), opts.data(), S->cfg.precision, &sz, false) != PGVIMP_OK) {
       if (cnt == 1) break;
       continue;
     }
@@ -326,8 +325,10 @@ void scheduler(pgvimp_server* S) {
       Flight* f = S->finished.back();
       S->finished.pop_back();
       lk.unlock();
+      const double tc = S->now_ms();
       collect_flight(f);
       lk.lock();
+      S->host_collect_ms += S->now_ms() - tc;
       const double t = S->now_ms();
       for (Request* r : f->reqs) {
         r->state = 2;
@@ -365,7 +366,9 @@ void scheduler(pgvimp_server* S) {
           S->launched_batches += 1;
           S->launched_plans += f->reqs.size();
           lk.unlock();
+          const double tl = S->now_ms();
           pgvimp_status st = launch_flight(S, f);
+          S->host_launch_ms += S->now_ms() - tl;
           if (st != PGVIMP_OK) {
             f->launch_status = st;
             const char* e = pgvimp_last_error(nullptr);
@@ -407,9 +410,9 @@ extern "C" pgvimp_status pgvimp_server_create(const pgvimp_server_config* cfg, p
   if (c.hbm_budget_bytes < ((size_t)1 << 20)) return server_fail(PGVIMP_EINVAL, "hbm_budget_bytes must be >= 1 MiB");
   if (c.max_inflight < 1 || c.max_inflight > 64) return server_fail(PGVIMP_EINVAL, "max_inflight must be in 1..64");
   if (c.max_batch < 1 || c.max_batch > (1 << 20)) return server_fail(PGVIMP_EINVAL, "max_batch must be >= 1");
-  if (c.plan_threads < 0 || (c.plan_threads > 1 && (c.plan_threads < 32 || c.plan_threads > kCrMaxThreads ||
-                                                     (c.plan_threads & 31))))
-    return server_fail(PGVIMP_EINVAL, "plan_threads must be 0, 1, or a multiple of 32 in 32..256");
+  if (c.plan_threads < -1 || (c.plan_threads > 1 && (c.plan_threads < 32 || c.plan_threads > kCrMaxThreads ||
+                                                      (c.plan_threads & 31))))
+    return server_fail(PGVIMP_EINVAL, "plan_threads must be -1, 0, 1, or a multiple of 32 in 32..256");
   if (!(c.batch_window_ms >= 0.0) || !(c.batch_window_ms < 1e7)) return server_fail(PGVIMP_EINVAL, "bad batch_window_ms");
   if (c.host_staging_bytes == 0) c.host_staging_bytes = std::min<size_t>(c.hbm_budget_bytes, (size_t)4 << 30);
   pgvimp_server* S = new (std::nothrow) pgvimp_server();
@@ -452,7 +455,8 @@ extern "C" pgvimp_status pgvimp_submit(pgvimp_server* S, const pgvimp_problem* p
                                        uint64_t* request_id) {
   if (!S || !problem || !options || !request_id) return server_fail(PGVIMP_EINVAL, "NULL argument");
   pgvimp_options o = *options;
-  o.plan_threads = S->cfg.plan_threads;
+  if (S->cfg.plan_threads >= 0) o.plan_threads = S->cfg.plan_threads;
+  if (o.plan_threads == 1) o.plan_threads = 0;
   BatchSizes sz;
   pgvimp_status st = batch_sizes(1, problem, &o, S->cfg.precision, &sz);   // validates the request
   if (st != PGVIMP_OK) return st;
@@ -463,7 +467,7 @@ extern "C" pgvimp_status pgvimp_submit(pgvimp_server* S, const pgvimp_problem* p
   r->prob.take(*problem);
   r->opt = o;
   const bool slr = problem->dyn_kind != PGVIMP_DYN_LINEAR;
-  r->key = GroupKey{problem->n, problem->dyn_kind, slr ? o.iters : 0, slr ? o.slr_iters : 0};
+  r->key = GroupKey{problem->n, problem->dyn_kind, slr ? o.iters : 0, slr ? o.slr_iters : 0, o.plan_threads};
   std::lock_guard<std::mutex> lk(S->mu);
   if (S->stop) {
     delete r;
@@ -523,6 +527,8 @@ extern "C" pgvimp_status pgvimp_server_stats(pgvimp_server* S, pgvimp_server_sta
   out->dev_used = S->dev_alloc.used();
   out->host_used = S->host_alloc.used();
   out->now_ms = S->now_ms();
+  out->host_launch_ms = S->host_launch_ms;
+  out->host_collect_ms = S->host_collect_ms;
   return PGVIMP_OK;
 }
 
