@@ -27,7 +27,7 @@ import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
-# The server overlaps batches on up to 16 streams; with CUDA's default of 8
+# The server overlaps batches on up to 32 streams; with CUDA's default of 8
 # hardware work queues, streams share queues and their kernels serialise.
 os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
 
@@ -259,7 +259,7 @@ def _pct(v, q):
     return float(np.percentile(np.asarray(v, dtype=float), q)) if len(v) else None
 
 
-def run_served(mix, precision, plan_threads, max_inflight=16, max_batch=32, window_ms=2.0, submitters=4):
+def run_served(mix, precision, plan_threads, max_inflight=32, max_batch=16, window_ms=2.0, submitters=4):
     """Replays the mix's arrival times against a server (continuous batching)
     and returns plans/s (count / time from the first arrival to the last
     result on the host) and p50/p99 latency (arrival to result on the host)."""

@@ -239,7 +239,10 @@ const char *pgvimp_last_error(const void *ctx);
  * others run overlap on the GPU.  A batch is admitted when a stream is free
  * and its device arena and pinned staging fit the server's pools, which are
  * allocated once at creation; a request waits at most `batch_window_ms` for
- * others to share its launch.  All server functions are thread-safe. */
+ * others to share its launch.  All server functions are thread-safe.
+ * Streams beyond the device's hardware work queues share queues and their
+ * kernels serialise: run the process with CUDA_DEVICE_MAX_CONNECTIONS >=
+ * max_inflight (at most 32) set before the CUDA context is created. */
 typedef struct pgvimp_server pgvimp_server;
 typedef struct {
   size_t hbm_budget_bytes;   /* device pool for admitted batches (>= 1 MiB) */

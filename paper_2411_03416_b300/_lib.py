@@ -377,7 +377,7 @@ class Server:
     continuous batching of independent plan requests on one GPU."""
 
     def __init__(self, hbm_budget_bytes: int, precision: int = PREC_MIXED, plan_threads: int = 64,
-                 max_inflight: int = 16, max_batch: int = 32, batch_window_ms: float = 2.0,
+                 max_inflight: int = 32, max_batch: int = 16, batch_window_ms: float = 2.0,
                  host_staging_bytes: int = 0):
         cfg = ServerConfig(hbm_budget_bytes, host_staging_bytes, precision, plan_threads, max_inflight, max_batch,
                            batch_window_ms)
