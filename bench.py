@@ -54,9 +54,12 @@ def plan_problem(i: int, base=None):
 
 
 def make_batch_problems(count: int, rank: int = 0):
+    """Rank r plans indices r*count .. r*count + count - 1 (disjoint across
+    replicas); each map is built once."""
     import workloads as W
-    base = [W.c2_point2d_dense(request=k, N=N_STEPS, iters=ITERS) for k in range(min(MAP_POOL, count))]
-    pairs = [plan_problem(rank * count + i, base) for i in range(count)]
+    idx = [rank * count + i for i in range(count)]
+    base = {k: W.c2_point2d_dense(request=k, N=N_STEPS, iters=ITERS) for k in sorted({j % MAP_POOL for j in idx})}
+    pairs = [plan_problem(j, base) for j in idx]
     return [p for p, _ in pairs], [o for _, o in pairs]
 
 
@@ -194,12 +197,15 @@ def cpu_baseline(workers: int | None = None, plans_per_worker: int = 1):
 # ------------------------------------------------------------------------ main
 
 def dist_init():
+    """Replicas: one process per GPU (NCCL), or gloo ranks on a host without
+    a GPU (the multi-rank host logic is tested that way)."""
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if ws > 1:
+        import torch
         import torch.distributed as dist
-        dist.init_process_group("nccl")
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     return ws, rank, local
 
 
@@ -214,7 +220,8 @@ def max_over_ranks(ws, v: float) -> float:
         return v
     import torch
     import torch.distributed as dist
-    t = torch.tensor([v], device="cuda", dtype=torch.float64)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([v], device=dev, dtype=torch.float64)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 

@@ -62,7 +62,7 @@ typedef enum {
   PGVIMP_DYN_PLANAR_QUAD = 1   /* f_0 of the planar quadrotor with u = 0, linearised by SLR (Alg. 2) */
 } pgvimp_dyn_kind;
 
-typedef enum { PGVIMP_RULE_GH = 0, PGVIMP_RULE_DEG3 = 1 } pgvimp_rule;
+typedef enum { PGVIMP_RULE_GH = 0, PGVIMP_RULE_DEG3 = 1, PGVIMP_RULE_SMOLYAK = 2 } pgvimp_rule;
 
 /* Arithmetic of the path.  PLAIN_FP64: everything in FP64.  MIXED: the
  * quadrature, SDF and moment arithmetic in FP32 (FP32 accumulation); the
@@ -109,7 +109,9 @@ typedef struct {
 } pgvimp_problem;
 
 typedef struct {
-  int rule;         /* pgvimp_rule: GH tensor rule (gh_p points per dim) or degree-3 (2n+1 points) */
+  int rule;         /* pgvimp_rule: GH tensor rule (gh_p points per dim), degree-3 (2n+1 points), or
+                       Smolyak sparse grid of level gh_p (Lemma 1: 1-D GH rules with 1..gh_p points,
+                       exact for total degree 2 gh_p - 1) */
   int gh_p;         /* 2..10 */
   double beta_max;  /* first trial step size (App. C), > 0 */
   double kl_eps;    /* KL bound epsilon (may be +inf) */
@@ -123,6 +125,11 @@ typedef struct {
                        32..256, a multiple of 32: one thread block of that size per plan, the block
                        recursions by cyclic reduction over time (latency form); PLAIN_FP64 or MIXED
                        precision only (EINVAL with MIXED_DF). */
+  double temperature_high; /* two-phase temperature (the low/high T-hat schedule of the planning
+                              experiments, Sec. 7): from global iteration switch_iter on (> 0), K^-1, b
+                              and the cost are divided by temperature_high (> 0) instead of the
+                              problem's temperature; 0 or switch_iter = 0: one phase */
+  int switch_iter;
 } pgvimp_options;
 
 /* Per-iteration record.  Costs are those of the iterate the gradients were

@@ -58,6 +58,7 @@ class _Options(C.Structure):
         ("rule", C.c_int), ("gh_p", C.c_int), ("beta_max", C.c_double), ("kl_eps", C.c_double),
         ("max_bisect", C.c_int), ("iters", C.c_int), ("slr_iters", C.c_int),
         ("init_kind", C.c_int), ("init_scale", C.c_double), ("replay_beta", C.c_void_p),
+        ("temperature_high", C.c_double), ("switch_iter", C.c_int),
     ]
 
 
@@ -140,6 +141,8 @@ class _Marshal:
             o.rule, o.gh_p, o.beta_max, o.kl_eps = op.rule, op.gh_p, op.beta_max, op.kl_eps
             o.max_bisect, o.iters, o.slr_iters = op.max_bisect, op.iters, op.slr_iters
             o.init_kind, o.init_scale = op.init_kind, op.init_scale
+            o.temperature_high = getattr(op, "temperature_high", 0.0)
+            o.switch_iter = getattr(op, "switch_iter", 0)
             if op.replay_beta is not None:
                 o.replay_beta = _ptr(self._k(_f64(op.replay_beta)))
             self.op = o

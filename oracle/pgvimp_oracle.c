@@ -195,8 +195,89 @@ int ora_gh_rule(int p, double *nodes, double *weights) {
   return ORA_OK;
 }
 
+/* Smolyak sparse grid of level k in d dimensions (Lemma 1): the combination
+ *   A(k, d) = sum_{q = max(0, k-d)}^{k-1} (-1)^{k-1-q} C(d-1, k-1-q)
+ *             sum_{i_1 + ... + i_d = d + q, i_j >= 1} U^{i_1} x ... x U^{i_d}
+ * of the 1-D Gauss-Hermite rules U^i with i points; exact for every
+ * polynomial of total degree <= 2k - 1.  Coinciding nodes are merged (their
+ * weights added).  Returns the node count; with xi == NULL only counts.
+ * Written out plainly: the multi-indices in lexicographic order (an entry
+ * grows only while the sum stays within d + k - 1), all tensor nodes of
+ * each, a linear search for duplicates. */
+static double binom(int a, int b) {
+  if (b < 0 || b > a) return 0.0;
+  double r = 1.0;
+  for (int j = 1; j <= b; ++j) r = r * (a - b + j) / j;
+  return r;
+}
+
+static int smolyak_grid(int d, int k, double *xi, double *W, int cap) {
+  double nodes[11][10], wts[11][10];
+  for (int p = 1; p <= k; ++p)
+    if (ora_gh_rule(p, nodes[p], wts[p])) return -1;
+  int count = 0;
+  double *X = malloc(sizeof(double) * (size_t)cap * d), *Wt = malloc(sizeof(double) * cap);
+  int *idx = malloc(sizeof(int) * d), *dig = malloc(sizeof(int) * d);
+  double *pt = malloc(sizeof(double) * d);
+  if (!X || !Wt || !idx || !dig || !pt) { count = -1; goto out; }
+  for (int j = 0; j < d; ++j) idx[j] = 1;
+  for (;;) {
+    int s = 0;
+    for (int j = 0; j < d; ++j) s += idx[j];
+    int q = s - d;
+    if (q >= (k > d ? k - d : 0) && q <= k - 1) {
+      double coef = (((k - 1 - q) % 2) ? -1.0 : 1.0) * binom(d - 1, k - 1 - q);
+      for (int j = 0; j < d; ++j) dig[j] = 0;
+      for (;;) {
+        double w = coef;
+        for (int j = 0; j < d; ++j) {
+          pt[j] = nodes[idx[j]][dig[j]];
+          w *= wts[idx[j]][dig[j]];
+        }
+        int found = -1;
+        for (int m = 0; m < count && found < 0; ++m) {
+          int same = 1;
+          for (int j = 0; j < d && same; ++j) same = (X[(size_t)m * d + j] == pt[j]);
+          if (same) found = m;
+        }
+        if (found >= 0) {
+          Wt[found] += w;
+        } else {
+          if (count == cap) { count = -1; goto out; }
+          memcpy(X + (size_t)count * d, pt, sizeof(double) * d);
+          Wt[count++] = w;
+        }
+        int j = d - 1;   /* next tensor node */
+        while (j >= 0 && ++dig[j] == idx[j]) dig[j--] = 0;
+        if (j < 0) break;
+      }
+    }
+    /* next multi-index with sum <= d + k - 1: raise the last entry that
+       can grow, reset the ones after it to 1 */
+    int j = d - 1;
+    for (; j >= 0; --j) {
+      int rest = 0;
+      for (int m = 0; m < d; ++m) rest += (m < j) ? idx[m] : 1;
+      if (rest + idx[j] + 1 - 1 <= d + k - 1 && idx[j] + 1 <= k) break;
+    }
+    if (j < 0) break;
+    ++idx[j];
+    for (int m = j + 1; m < d; ++m) idx[m] = 1;
+  }
+  if (xi) {
+    memcpy(xi, X, sizeof(double) * (size_t)count * d);
+    memcpy(W, Wt, sizeof(double) * count);
+  }
+out:
+  free(X); free(Wt); free(idx); free(dig); free(pt);
+  return count;
+}
+
+static const int kSmolyakCap = 200000;
+
 int ora_rule_size(int n, int rule, int p) {
   if (rule == ORA_RULE_DEG3) return 2 * n + 1;
+  if (rule == ORA_RULE_SMOLYAK) return smolyak_grid(n, p, NULL, NULL, kSmolyakCap);
   int s = 1;
   for (int j = 0; j < n; ++j) s *= p;
   return s;
@@ -207,6 +288,7 @@ int ora_rule_size(int n, int rule, int p) {
  * Degree 3 (Lemma 1's sparse family, its lowest level): {0, +-sqrt(3) e_j},
  * weights 1 - n/3 and 1/6; order: centre, then +e_0, -e_0, +e_1, ... */
 int ora_rule(int n, int rule, int p, double *xi, double *W) {
+  if (rule == ORA_RULE_SMOLYAK) return smolyak_grid(n, p, xi, W, kSmolyakCap) < 0 ? ORA_EINVAL : ORA_OK;
   if (rule == ORA_RULE_DEG3) {
     memset(xi, 0, sizeof(double) * (2 * n + 1) * n);
     W[0] = 1.0 - n / 3.0;
@@ -802,8 +884,16 @@ done:
   return rc;
 }
 
+/* The problem at global iteration k: the problem itself, or, from the
+ * temperature switch on, a copy with T-hat = temperature_high. */
+static int hot_phase(const ora_options *op, int k) {
+  return op->switch_iter > 0 && op->temperature_high > 0.0 && k >= op->switch_iter;
+}
+
 /* Alg. 1: prior, initial iterate (init != 0) or the given (mu, Lambda), its
- * marginals, then op->iters proximal iterations. */
+ * marginals, then op->iters proximal iterations.  At the temperature switch
+ * the prior (K^-1, b) is rebuilt at the high temperature and the cost is
+ * divided by it from then on. */
 int ora_plan(const ora_problem *pb, const ora_options *op, int init, double *mu, double *Ld,
              double *Lo, double *Sd, double *So, ora_iter_log *logs) {
   int n = pb->n, N = pb->N;
@@ -828,9 +918,20 @@ int ora_plan(const ora_problem *pb, const ora_options *op, int init, double *mu,
     }
   }
   if ((rc = ora_marginals(n, N, Ld, Lo, Sd, So, &logdet))) goto done;
-  for (int k = 0; k < op->iters; ++k)
-    if ((rc = ora_step(pb, op, k, Kd, Ko, b, mubar, mu, Ld, Lo, Sd, So, &logdet, logs ? logs + k : NULL)))
-      goto done;
+  {
+    ora_problem hot = *pb;
+    hot.temperature = op->temperature_high;
+    const ora_problem *cur = pb;
+    for (int k = 0; k < op->iters; ++k) {
+      if (hot_phase(op, k) && cur == pb) {
+        cur = &hot;
+        if ((rc = ora_prior(cur, NULL, NULL, Kd, Ko, b, NULL, NULL, NULL))) goto done;
+        if ((rc = ora_prior_mean(cur, Kd, Ko, b, mubar))) goto done;
+      }
+      if ((rc = ora_step(cur, op, k, Kd, Ko, b, mubar, mu, Ld, Lo, Sd, So, &logdet, logs ? logs + k : NULL)))
+        goto done;
+    }
+  }
 done:
   free(Kd); free(Ko); free(b); free(mubar);
   return rc;
@@ -933,20 +1034,29 @@ int ora_plan_slr(const ora_problem *pb, const ora_options *op, double *mu, doubl
   ora_init_mean(pb, xbar);
   ora_init_mean(pb, mu);
   for (int i = 0; i <= N; ++i) memcpy(Sbar + i * nn, pb->K0, sizeof(double) * nn);
+  ora_problem hot = *pb;
+  hot.temperature = op->temperature_high;
   for (int j = 0; j < op->slr_iters; ++j) {
     double logdet;
+    const ora_problem *cur = hot_phase(op, j * op->iters) ? &hot : pb;
     if ((rc = ora_slr(pb, op, xbar, Sbar, Al, al))) goto done;
-    if ((rc = ora_prior(pb, Al, al, Kd, Ko, b, NULL, NULL, NULL))) goto done;
-    if ((rc = ora_prior_mean(pb, Kd, Ko, b, mubar))) goto done;
+    if ((rc = ora_prior(cur, Al, al, Kd, Ko, b, NULL, NULL, NULL))) goto done;
+    if ((rc = ora_prior_mean(cur, Kd, Ko, b, mubar))) goto done;
     if (j == 0) {
       memcpy(Ld, Kd, sizeof(double) * (N + 1) * nn);
       memcpy(Lo, Ko, sizeof(double) * N * nn);
     }
     if ((rc = ora_marginals(n, N, Ld, Lo, Sd, So, &logdet))) goto done;
-    for (int k = 0; k < op->iters; ++k)
-      if ((rc = ora_step(pb, op, j * op->iters + k, Kd, Ko, b, mubar, mu, Ld, Lo, Sd, So, &logdet,
+    for (int k = 0; k < op->iters; ++k) {
+      if (hot_phase(op, j * op->iters + k) && cur == pb) {   /* switch inside this linearisation */
+        cur = &hot;
+        if ((rc = ora_prior(cur, Al, al, Kd, Ko, b, NULL, NULL, NULL))) goto done;
+        if ((rc = ora_prior_mean(cur, Kd, Ko, b, mubar))) goto done;
+      }
+      if ((rc = ora_step(cur, op, j * op->iters + k, Kd, Ko, b, mubar, mu, Ld, Lo, Sd, So, &logdet,
                          logs ? logs + (size_t)j * op->iters + k : NULL)))
         goto done;
+    }
     double s = 0.0;
     for (int e = 0; e < D; ++e) s += (mu[e] - xbar[e]) * (mu[e] - xbar[e]);
     if (slr_norms) slr_norms[j] = sqrt(s);

@@ -29,7 +29,7 @@ extern "C" {
 
 enum { ORA_COST_NONE = 0, ORA_COST_POINT2D = 1, ORA_COST_POINT3D = 2, ORA_COST_ARM = 3, ORA_COST_QUADRATIC = 4 };
 enum { ORA_DYN_LINEAR = 0, ORA_DYN_PLANAR_QUAD = 1, ORA_DYN_AFFINE_TEST = 2 };
-enum { ORA_RULE_GH = 0, ORA_RULE_DEG3 = 1 };
+enum { ORA_RULE_GH = 0, ORA_RULE_DEG3 = 1, ORA_RULE_SMOLYAK = 2 };
 enum { ORA_OK = 0, ORA_EINVAL = 1, ORA_ENOTPD = 2, ORA_ENOMEM = 3 };
 
 typedef struct {
@@ -71,7 +71,8 @@ typedef struct {
 } ora_problem;
 
 typedef struct {
-  int rule;                 /* ORA_RULE_GH (tensor, gh_p points per dim) or ORA_RULE_DEG3 */
+  int rule;                 /* ORA_RULE_GH (tensor, gh_p points per dim), ORA_RULE_DEG3, or
+                               ORA_RULE_SMOLYAK (sparse grid of level gh_p, Lemma 1) */
   int gh_p;
   double beta_max;          /* first trial step size */
   double kl_eps;            /* KL bound (may be +inf) */
@@ -81,6 +82,11 @@ typedef struct {
   int init_kind;            /* 0: Lambda0 = K^-1; 1: Lambda0 = init_scale * I */
   double init_scale;
   const double *replay_beta;/* if non-NULL: take these beta_k (no search, no KL test) */
+  /* two-phase temperature (the planning experiments of Sec. 7 run a low, then
+     a high temperature): from global iteration switch_iter on (> 0), T-hat =
+     temperature_high (> 0) in place of the problem's temperature */
+  double temperature_high;
+  int switch_iter;
 } ora_options;
 
 typedef struct {

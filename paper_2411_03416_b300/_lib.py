@@ -62,7 +62,8 @@ class Options(C.Structure):
     _fields_ = [
         ("rule", C.c_int), ("gh_p", C.c_int), ("beta_max", C.c_double), ("kl_eps", C.c_double),
         ("max_bisect", C.c_int), ("iters", C.c_int), ("slr_iters", C.c_int), ("init_kind", C.c_int),
-        ("init_scale", C.c_double), ("plan_threads", C.c_int),
+        ("init_scale", C.c_double), ("plan_threads", C.c_int), ("temperature_high", C.c_double),
+        ("switch_iter", C.c_int),
     ]
 
 
@@ -207,6 +208,8 @@ def marshal_options(op) -> Options:
     o.max_bisect, o.iters, o.slr_iters = op.max_bisect, op.iters, op.slr_iters
     o.init_kind, o.init_scale = op.init_kind, op.init_scale
     o.plan_threads = getattr(op, "plan_threads", 0)
+    o.temperature_high = getattr(op, "temperature_high", 0.0)
+    o.switch_iter = getattr(op, "switch_iter", 0)
     return o
 
 

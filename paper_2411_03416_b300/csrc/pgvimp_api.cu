@@ -7,8 +7,10 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <functional>
 #include <map>
 #include <mutex>
+#include <tuple>
 #include <string>
 #include <vector>
 
@@ -140,6 +142,94 @@ void ensure_tables() {
   g_tables_ready = true;
 }
 
+// ------------------------------------------------------------ sparse grids
+
+// Smolyak sparse grid of level k over d dimensions (Lemma 1), built from the
+// 1-D Gauss-Hermite rules with i = 1..k points by the combination formula
+//   sum over multi-indices i >= 1 with d + max(0, k - d) <= |i| <= d + k - 1
+//   of (-1)^(d + k - 1 - |i|) C(d - 1, d + k - 1 - |i|) U^{i_1} x ... x U^{i_d};
+// exact for total degree 2k - 1.  Coinciding nodes (to 1e-12) are merged.
+// `add` receives each (node, weight) of the combination.
+struct GridKey {
+  std::vector<long long> q;
+  bool operator<(const GridKey& o) const { return q < o.q; }
+};
+
+void smolyak_terms(int d, int k, const std::function<void(const double*, double)>& add) {
+  std::vector<int> idx(d, 1), dig(d, 0);
+  std::vector<double> pt(d);
+  const int top = d + k - 1, low = d + std::max(0, k - d);
+  std::function<void(int, int)> rec = [&](int j, int sum) {
+    if (j == d) {
+      if (sum < low) return;
+      const int m = top - sum;
+      double c = (m % 2) ? -1.0 : 1.0;
+      for (int t = 1; t <= m; ++t) c = c * (d - 1 - m + t) / t;   // C(d-1, m)
+      std::fill(dig.begin(), dig.end(), 0);
+      for (;;) {
+        double w = c;
+        for (int a = 0; a < d; ++a) {
+          pt[a] = g_gh_x[idx[a] * kMaxGH + dig[a]];
+          w *= g_gh_w[idx[a] * kMaxGH + dig[a]];
+        }
+        add(pt.data(), w);
+        int a = d - 1;
+        while (a >= 0 && ++dig[a] == idx[a]) dig[a--] = 0;
+        if (a < 0) break;
+      }
+      return;
+    }
+    for (int i = 1; i <= k && sum + i + (d - 1 - j) <= top; ++i) {
+      idx[j] = i;
+      rec(j + 1, sum + i);
+    }
+  };
+  rec(0, 0);
+}
+
+// Number of multi-indices and of (unmerged) nodes of the level-k grid.
+void smolyak_size(int d, int k, double* terms, double* nodes) {
+  *terms = 0.0;
+  *nodes = 0.0;
+  std::function<void(int, int, double)> rec = [&](int j, int sum, double prod) {
+    if (*terms > 1e7) return;
+    if (j == d) {
+      if (sum >= d + std::max(0, k - d)) {
+        *terms += 1.0;
+        *nodes += prod;
+      }
+      return;
+    }
+    for (int i = 1; i <= k && sum + i + (d - 1 - j) <= d + k - 1; ++i) rec(j + 1, sum + i, prod * i);
+  };
+  rec(0, 0, 1.0);
+}
+
+// Merged table with `cols` weight columns: column c holds the level (k - c) grid.
+std::vector<double> sparse_table(int d, int k, int cols) {
+  ensure_tables();
+  std::map<GridKey, std::vector<double>> pts;
+  for (int c = 0; c < cols; ++c) {
+    if (k - c < 1) continue;
+    smolyak_terms(d, k - c, [&](const double* x, double w) {
+      GridKey key;
+      key.q.resize(d);
+      for (int a = 0; a < d; ++a) key.q[a] = std::llround(x[a] * 1e12);
+      auto it = pts.find(key);
+      if (it == pts.end()) {
+        std::vector<double> row(d + cols, 0.0);
+        for (int a = 0; a < d; ++a) row[a] = x[a];
+        it = pts.emplace(key, row).first;
+      }
+      it->second[d + c] += w;
+    });
+  }
+  std::vector<double> out;
+  out.reserve(pts.size() * (d + cols));
+  for (auto& kv : pts) out.insert(out.end(), kv.second.begin(), kv.second.end());
+  return out;
+}
+
 // ------------------------------------------------------------ validation
 
 bool finite_all(const double* p, size_t k) {
@@ -232,7 +322,14 @@ pgvimp_status validate(const pgvimp_problem& p, const pgvimp_options& o, int idx
         !finite_all(p.sphere_r, p.n_spheres))
       return E(PGVIMP_ENOTFINITE, "arm model not finite");
   }
-  if (o.rule != PGVIMP_RULE_GH && o.rule != PGVIMP_RULE_DEG3) return E(PGVIMP_EINVAL, "unknown rule");
+  if (o.rule != PGVIMP_RULE_GH && o.rule != PGVIMP_RULE_DEG3 && o.rule != PGVIMP_RULE_SMOLYAK)
+    return E(PGVIMP_EINVAL, "unknown rule");
+  if (o.rule == PGVIMP_RULE_SMOLYAK) {
+    if (o.gh_p < 2 || o.gh_p > kMaxGH) return E(PGVIMP_EINVAL, "Smolyak level (gh_p) must be in 2..10");
+    double terms, nodes;
+    smolyak_size(std::max(dc, p.dyn_kind != PGVIMP_DYN_LINEAR ? n : 0), o.gh_p, &terms, &nodes);
+    if (terms > 1e5 || nodes > 2e5) return E(PGVIMP_EINVAL, "sparse grid too large");
+  }
   if (o.rule == PGVIMP_RULE_GH) {
     if (o.gh_p < 2 || o.gh_p > kMaxGH) return E(PGVIMP_EINVAL, "gh_p must be in 2..10");
     double pts = std::pow((double)o.gh_p, (double)std::max(dc, p.dyn_kind != PGVIMP_DYN_LINEAR ? n : 0));
@@ -246,6 +343,8 @@ pgvimp_status validate(const pgvimp_problem& p, const pgvimp_options& o, int idx
   if (o.plan_threads > 1 && (o.plan_threads < 32 || o.plan_threads > kCrMaxThreads || (o.plan_threads & 31)))
     return E(PGVIMP_EINVAL, "plan_threads must be 0, 1, or a multiple of 32 in 32..256");
   if (o.plan_threads < 0) return E(PGVIMP_EINVAL, "plan_threads must be 0, 1, or a multiple of 32 in 32..256");
+  if (!(o.temperature_high >= 0.0) || !std::isfinite(o.temperature_high) || o.switch_iter < 0)
+    return E(PGVIMP_EINVAL, "temperature_high must be finite and >= 0, switch_iter >= 0");
   return PGVIMP_OK;
 }
 
@@ -260,6 +359,8 @@ struct PlanLayout {
   size_t Kd, Ko, b, mubar, mu1, Sd1, So1, mu2, Sd2, So2, g, G, Altv, altv, xbar, scr;  // WORK
   size_t A_cnt, a_cnt, sdf_cnt;
   bool sdf_owner;   // false: the grid is shared with an earlier plan of the batch
+  size_t sg, sgs;   // Smolyak tables (INPUT offsets), shared by plans with the same rule
+  int sg_rows, sgs_rows;
   int log_cap, slr_cap;
 };
 
@@ -271,6 +372,9 @@ struct BatchImpl {
   std::vector<pgvimp_options> opts;
   std::vector<PlanLayout> lay;
   std::vector<PlanDesc> desc;
+  // sparse-grid tables of the batch by (dimension, level, weight columns):
+  // INPUT offset and contents
+  std::map<std::tuple<int, int, int>, std::pair<size_t, std::vector<double>>> grids;
   size_t in_bytes = 0, res_bytes = 0, extra_bytes = 0, work_bytes = 0;
   size_t off_desc = 0, off_gh = 0, off_scal = 0, off_log = 0, off_slrn = 0;
   char* arena = nullptr;
@@ -346,6 +450,24 @@ void plan_layout(BatchImpl& B) {
     L.dh = take(in, 8 * std::max<size_t>(4 * dof, 1));
     L.soff = take(in, 8 * std::max<size_t>(3 * S, 1));
     L.srad = take(in, 8 * std::max<size_t>(S, 1));
+    L.sg = L.sgs = 0;
+    L.sg_rows = L.sgs_rows = 0;
+    if (B.opts[i].rule == PGVIMP_RULE_SMOLYAK) {
+      auto table = [&](int d, int k, int cols, size_t* off, int* rows) {
+        auto key = std::make_tuple(d, k, cols);
+        auto it = B.grids.find(key);
+        if (it == B.grids.end()) {
+          std::vector<double> t = sparse_table(d, k, cols);
+          size_t o = take(in, 8 * std::max<size_t>(t.size(), 2));
+          it = B.grids.emplace(key, std::make_pair(o, std::move(t))).first;
+        }
+        *off = it->second.first;
+        *rows = (int)(it->second.second.size() / (d + cols));
+      };
+      const int dc = cost_dims(p);
+      if (p.cost_kind != PGVIMP_COST_NONE && dc > 0) table(dc, B.opts[i].gh_p, 2, &L.sg, &L.sg_rows);
+      if (p.dyn_kind != PGVIMP_DYN_LINEAR) table((int)n, B.opts[i].gh_p, 1, &L.sgs, &L.sgs_rows);
+    }
     L.sdf_owner = true;
     if (L.sdf_cnt) {
       auto key = std::make_pair(p.sdf, L.sdf_cnt);
@@ -412,6 +534,8 @@ void build_descs(BatchImpl& B) {
     d.beta_max = o.beta_max; d.kl_eps = o.kl_eps; d.init_scale = o.init_scale;
     d.cost_kind = p.cost_kind; d.psi_form = p.psi_form; d.factor_set = p.factor_set;
     d.eps = p.eps; d.sigma_obs = p.sigma_obs; d.inv_temp = (p.temperature > 0.0) ? 1.0 / p.temperature : 1.0;
+    d.inv_temp_high = (o.temperature_high > 0.0 && o.switch_iter > 0) ? 1.0 / o.temperature_high : 0.0;
+    d.switch_iter = o.switch_iter;
     d.nx = p.sdf_nx; d.ny = p.sdf_ny; d.nz = std::max(p.sdf_nz, 1);
     for (int k = 0; k < 3; ++k) d.sdf_origin[k] = p.sdf_origin[k];
     d.cell = p.sdf_cell; d.inv_cell = p.sdf_cell > 0 ? 1.0 / p.sdf_cell : 0.0;
@@ -429,6 +553,10 @@ void build_descs(BatchImpl& B) {
           for (int k = 0; k < p.n_spheres; ++k) c += (p.sphere_link[k] == j);
       }
     }
+    d.sg = reinterpret_cast<const double*>(din + L.sg);
+    d.sgs = reinterpret_cast<const double*>(din + L.sgs);
+    d.sg_rows = L.sg_rows;
+    d.sgs_rows = L.sgs_rows;
     d.gh_x = reinterpret_cast<const double*>(din + B.off_gh);
     d.gh_w = d.gh_x + (kMaxGH + 1) * kMaxGH;
     d.dyn_kind = p.dyn_kind;
@@ -467,6 +595,9 @@ void stage_inputs(BatchImpl& B) {
   std::memcpy(h + B.off_desc, B.desc.data(), sizeof(PlanDesc) * B.count);
   std::memcpy(h + B.off_gh, g_gh_x, sizeof(g_gh_x));
   std::memcpy(h + B.off_gh + sizeof(g_gh_x), g_gh_w, sizeof(g_gh_w));
+  for (auto& kv : B.grids)
+    if (!kv.second.second.empty())
+      std::memcpy(h + kv.second.first, kv.second.second.data(), 8 * kv.second.second.size());
   for (int i = 0; i < B.count; ++i) {
     const pgvimp_problem& p = B.probs[i];
     const PlanLayout& L = B.lay[i];

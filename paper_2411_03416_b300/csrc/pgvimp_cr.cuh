@@ -583,6 +583,11 @@ template <int n, typename QT, typename R>
 PGV_BIG void cr_iterate_once(const PlanDesc& P, double* red) {
   constexpr int nn = n * n;
   double* sc = P.scal;
+  if (temp_switch_due(P)) {            // uniform: every thread reads the same slots
+    __syncthreads();
+    switch_temperature<n, R>(P, threadIdx.x, blockDim.x);
+    __syncthreads();
+  }
   const int cur = (int)sc[S_CUR];
   const int oa = (cur + 1) % 3, ob = (cur + 2) % 3;
   const int N = P.N;
@@ -835,7 +840,7 @@ __global__ void __launch_bounds__(kCrMaxThreads) k_prior_ltv_cta(const PlanDesc*
     }
   }
   ok = __syncthreads_and(ok);
-  const double it = P.inv_temp;
+  const double it = cur_inv_temp(P);
   R* Kd = rp<R>(P.Kd);
   R* Ko = rp<R>(P.Ko);
   R* b = rp<R>(P.b);
@@ -908,6 +913,7 @@ __global__ void __launch_bounds__(kCrMaxThreads) k_prior_ltv_cta(const PlanDesc*
   }
   ok = __syncthreads_and(ok);
   if (threadIdx.x == 0) {
+    P.scal[S_THIGH] = (P.inv_temp_high > 0.0 && it == P.inv_temp_high) ? 1.0 : 0.0;
     if (ok) ok = bt_solve<n, R>(P, Kd, Ko, b, rp<R>(P.mubar));
     if (!ok) P.scal[S_STATUS] = 1.0;
   }

@@ -172,6 +172,12 @@ PGV_BIG bool bt_solve(const PlanDesc& P, const R* Md, const R* Mo, const R* r, R
   return ok;
 }
 
+// Inverse temperature at the plan's current global iteration: the problem's
+// T-hat, or the high temperature from iteration switch_iter on.
+PGV_DEV double cur_inv_temp(const PlanDesc& P) {
+  return (P.inv_temp_high > 0.0 && P.scal[S_K] >= (double)P.switch_iter) ? P.inv_temp_high : P.inv_temp;
+}
+
 // Prior precision K^-1 (block tridiagonal), information vector b = K^-1 mu_bar
 // and mu_bar, for the LTI / LTV system given by (A, a) or, with `use_ltv`, by
 // the SLR linearisation (Altv, altv).  FP64 throughout; stored as R.
@@ -203,7 +209,8 @@ PGV_BIG bool prior_build(const PlanDesc& P, bool use_ltv) {
       carry_b[a] = s;
     }
   }
-  const double it = P.inv_temp;
+  const double it = cur_inv_temp(P);
+  P.scal[S_THIGH] = (P.inv_temp_high > 0.0 && it == P.inv_temp_high) ? 1.0 : 0.0;
   for (int i = 0; i < N; ++i) {
     if (i == 0 || !lti) {
       const double* Ai = use_ltv ? P.Altv + (size_t)i * nn : (P.A_per_step ? P.A + (size_t)i * nn : P.A);
@@ -432,7 +439,10 @@ PGV_DEV void grid_split(df64 mu, double origin, double inv_cell, int& base, QT& 
 // xi_0..xi_{dc-1} only, so the quadrature runs over the dc-dimensional rule in
 // xi-space: g = L^-T E[xi psi], G = 1/2 L^-T (E[xi xi^T psi] - E[psi] I) L^-1,
 // the trailing moments being known in closed form (tensor GH: xi_b is
-// independent of psi; degree 3: the +-sqrt(3) e_b points evaluate psi(mu)).
+// independent of psi; degree 3: the +-sqrt(3) e_b points evaluate psi(mu);
+// Smolyak of level k: the n-dimensional grid restricted to the dc cost
+// coordinates is the dc-dimensional grid of the same level, and a trailing
+// xi_b^2 psi integrates to the level k-1 value).
 template <int n, typename QT, typename R>
 PGV_DEV bool quad_factor(const PlanDesc& P, int i, const R* mu_i, const R* S_ii, R* g, R* G, double& M0_out) {
   constexpr int nn = n * n;
@@ -443,7 +453,8 @@ PGV_DEV bool quad_factor(const PlanDesc& P, int i, const R* mu_i, const R* S_ii,
   if (P.cost_kind == PGVIMP_COST_NONE || (P.factor_set == 1 && (i == 0 || i == P.N))) return true;
   const int dc = P.dc;
   const bool deg3 = (P.rule == PGVIMP_RULE_DEG3);
-  const int dL = deg3 ? n : dc;
+  const bool sparse = (P.rule == PGVIMP_RULE_SMOLYAK);
+  const int dL = (deg3 || sparse) ? n : dc;
   R L[nn], Li[nn];
   if (!chol_lead<n, R>(S_ii, dL, L, Li)) return false;
   QT Lq[nn], mua[kMaxN];
@@ -457,7 +468,28 @@ PGV_DEV bool quad_factor(const PlanDesc& P, int i, const R* mu_i, const R* S_ii,
   for (int a = 0; a < dc; ++a) M1[a] = 0;
   for (int e = 0; e < dc * dc; ++e) M2[e] = 0;
   QT dx[kMaxN], psi_c = 0;
-  if (!deg3) {
+  if (sparse) {
+    const int cols = dc + 2;
+    for (int l = 0; l < P.sg_rows; ++l) {
+      const double* row = P.sg + (size_t)l * cols;
+      QT xi[kMaxN];
+      for (int a = 0; a < dc; ++a) xi[a] = (QT)row[a];
+      for (int a = 0; a < dc; ++a) {
+        QT s = 0;
+        for (int c = 0; c <= a; ++c) s += Lq[a * n + c] * xi[c];
+        dx[a] = s;
+      }
+      const QT ps = point_psi<QT>(P, gb, gf, dx, mua);
+      const QT wp = (QT)row[dc] * ps;
+      psi_c += (QT)row[dc + 1] * ps;          // level k-1: the trailing second moments
+      M0 += wp;
+      for (int a = 0; a < dc; ++a) {
+        QT t = wp * xi[a];
+        M1[a] += t;
+        for (int c = 0; c <= a; ++c) M2[a * dc + c] += t * xi[c];
+      }
+    }
+  } else if (!deg3) {
     const int p = P.gh_p;
     int Pn = 1;
     for (int a = 0; a < dc; ++a) Pn *= p;
@@ -501,7 +533,7 @@ PGV_DEV bool quad_factor(const PlanDesc& P, int i, const R* mu_i, const R* S_ii,
   }
   // gradient assembly: D = blockdiag(M2 - M0 I, (psi_c - M0) I [degree 3 only]);
   // the cost is divided by the temperature T-hat
-  const double it = P.inv_temp;
+  const double it = cur_inv_temp(P);
   R D[nn];
   for (int e = 0; e < nn; ++e) D[e] = zero;
   const double m0 = (double)M0 * it;
@@ -513,7 +545,7 @@ PGV_DEV bool quad_factor(const PlanDesc& P, int i, const R* mu_i, const R* S_ii,
       D[a * n + c] = v;
       D[c * n + a] = v;
     }
-  if (deg3)
+  if (deg3 || sparse)
     for (int b = dc; b < n; ++b) D[b * n + b] = r_from<R>((double)psi_c * it) - m0r;
   for (int r = 0; r < dL; ++r) {
     R s = zero;
@@ -848,6 +880,34 @@ PGV_BIG TrialOut trial(const PlanDesc& P, double beta_d, int cur, int out, doubl
   return res;
 }
 
+// Two-phase temperature: when the plan reaches iteration switch_iter with a
+// prior still at the low temperature, K^-1 and b (built with 1/T_low) are
+// scaled by T_low/T_high -- the prior rebuilt at T_high -- and so is the prior
+// cost of the current iterate; mu_bar = K b does not change.  States i =
+// first, first + stride, ... (all of them for one thread).
+PGV_DEV bool temp_switch_due(const PlanDesc& P) {
+  return P.inv_temp_high > 0.0 && P.scal[S_K] >= (double)P.switch_iter && P.scal[S_THIGH] == 0.0;
+}
+template <int n, typename R>
+PGV_BIG void switch_temperature(const PlanDesc& P, int first, int stride) {
+  constexpr int nn = n * n;
+  const int N = P.N;
+  const R f = r_from<R>(P.inv_temp_high / P.inv_temp);
+  R* Kd = rp<R>(P.Kd);
+  R* Ko = rp<R>(P.Ko);
+  R* b = rp<R>(P.b);
+  for (int i = first; i <= N; i += stride) {
+    for (int e = 0; e < nn; ++e) Kd[(size_t)i * nn + e] = f * Kd[(size_t)i * nn + e];
+    if (i < N)
+      for (int e = 0; e < nn; ++e) Ko[(size_t)i * nn + e] = f * Ko[(size_t)i * nn + e];
+    for (int a = 0; a < n; ++a) b[(size_t)i * n + a] = f * b[(size_t)i * n + a];
+  }
+  if (first == 0) {   // done by one thread; block callers synchronise before reading it
+    P.scal[S_PRIOR] = P.scal[S_PRIOR] * (P.inv_temp_high / P.inv_temp);
+    P.scal[S_THIGH] = 1.0;
+  }
+}
+
 // Lambda_{k+1} = A~(beta) / (beta+1), written over (Ld, Lo).
 template <int n, typename R>
 PGV_BIG void accept_precision(const PlanDesc& P, double beta_d) {
@@ -884,6 +944,7 @@ PGV_BIG void accept_precision(const PlanDesc& P, double beta_d) {
 template <int n, typename QT, typename R>
 PGV_BIG void iterate_once(const PlanDesc& P) {
   double* sc = P.scal;
+  if (temp_switch_due(P)) switch_temperature<n, R>(P, 0, 1);
   const int cur = (int)sc[S_CUR];
   const int oa = (cur + 1) % 3, ob = (cur + 2) % 3;
   double coll;
@@ -1046,7 +1107,14 @@ PGV_DEV bool slr_step(const PlanDesc& P, const double* xbar, const double* Sbar,
       for (int c = 0; c < n; ++c) F1[a * n + c] += wf * xi[c];
     }
   };
-  if (P.rule == PGVIMP_RULE_DEG3) {
+  if (P.rule == PGVIMP_RULE_SMOLYAK) {
+    for (int l = 0; l < P.sgs_rows; ++l) {
+      const double* row = P.sgs + (size_t)l * (n + 1);
+      QT xi[n];
+      for (int a = 0; a < n; ++a) xi[a] = (QT)row[a];
+      accum(xi, (QT)row[n]);
+    }
+  } else if (P.rule == PGVIMP_RULE_DEG3) {
     QT xi[n];
     for (int a = 0; a < n; ++a) xi[a] = 0;
     accum(xi, (QT)(1.0 - n / 3.0));

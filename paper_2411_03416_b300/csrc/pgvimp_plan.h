@@ -37,7 +37,8 @@ enum ScalSlot {
   S_T_TRACE = 14,     // tr((Lambda_k - Lambda') Sigma') of the last trial
   S_T_BEST = 15,      // best-feasible buffer set during a search
   S_NSETS = 16,
-  S_FMT = 17           // double-float storage: 1 while the result buffers hold FP64
+  S_FMT = 17,          // double-float storage: 1 while the result buffers hold FP64
+  S_THIGH = 18         // 1 once K^-1 and b are divided by the high temperature
 };
 
 // Sets the calling thread's error text returned by pgvimp_last_error(NULL).
@@ -60,6 +61,8 @@ struct PlanDesc {
   // cost
   int cost_kind, psi_form, factor_set;
   double eps, sigma_obs, inv_temp;
+  double inv_temp_high;        // 1 / high temperature from iteration switch_iter on (0: one phase)
+  int switch_iter;
   int nx, ny, nz;
   double sdf_origin[3];
   double cell, inv_cell;
@@ -72,6 +75,12 @@ struct PlanDesc {
   // Gauss-Hermite tables: nodes / weights of the p-point rule at [p * kMaxGH + j]
   const double* gh_x;
   const double* gh_w;
+  // Smolyak rule tables (rule SMOLYAK): the collision rule over the dc cost
+  // coordinates, rows (xi_0..xi_{dc-1}, weight at level k, weight at level
+  // k-1), and for SLR plans the rule over all n dimensions, rows (xi, weight)
+  const double* sg;
+  const double* sgs;
+  int sg_rows, sgs_rows;
   // prior inputs
   int dyn_kind;
   double dyn_params[4];

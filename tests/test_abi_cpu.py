@@ -128,3 +128,23 @@ def test_plan_threads_validation(pg):
     assert st == _lib.EINVAL
     # the block form runs FP64 or mixed recursions, not double-float
     assert _arena_status(pg, pb, replace(op, plan_threads=64), precision=2)[0] == _lib.EINVAL
+
+
+def test_temperature_schedule_validation(pg):
+    from paper_2411_03416_b300 import _lib
+    pb, op = W.c1_point2d()
+    assert _arena_status(pg, pb, replace(op, temperature_high=10.0, switch_iter=5))[0] == 0
+    assert _arena_status(pg, pb, replace(op, temperature_high=-1.0, switch_iter=5))[0] == _lib.EINVAL
+    assert _arena_status(pg, pb, replace(op, temperature_high=float("inf"), switch_iter=5))[0] == _lib.EINVAL
+    assert _arena_status(pg, pb, replace(op, temperature_high=10.0, switch_iter=-2))[0] == _lib.EINVAL
+
+
+def test_smolyak_validation(pg):
+    from paper_2411_03416_b300 import _lib
+    pb, op = W.c1_point2d()
+    assert _arena_status(pg, pb, replace(op, rule=W.RULE_SMOLYAK, gh_p=3))[0] == 0
+    assert _arena_status(pg, pb, replace(op, rule=W.RULE_SMOLYAK, gh_p=1))[0] == _lib.EINVAL
+    assert _arena_status(pg, pb, replace(op, rule=7))[0] == _lib.EINVAL
+    arm, aop = W.c3_arm(N=20)
+    assert _arena_status(pg, arm, replace(aop, rule=W.RULE_SMOLYAK, gh_p=3))[0] == 0
+    assert _arena_status(pg, arm, replace(aop, rule=W.RULE_SMOLYAK, gh_p=10))[0] == _lib.EINVAL   # too large

@@ -218,3 +218,81 @@ def test_double_float_run_continues_after_download(pg):
     res = gpu_solve([pb], [op], MIXED_DF)[0]
     assert np.linalg.norm(mu6 - res.mu) <= 1e-9 * np.linalg.norm(res.mu)
     assert np.linalg.norm(mu3 - res.mu) > 0
+
+
+# ------------------------------------------------------- 3-D point robot (n = 6)
+
+@pytest.mark.parametrize("prec,tol", [(FP64, TOL_FP64_SMALL), (MIXED, TOL_MIXED), (MIXED_DF, TOL_MIXED)])
+def test_point3d_thread_form(pg, prec, tol):
+    """Trilinear SDF lookups with the point-robot hinge, 27 distinct sigma
+    points on the three position coordinates (the oracle runs all 729)."""
+    pb, op = W.point3d()
+    res = gpu_solve([pb], [op], prec)[0]
+    compare_plan(pb, op, res, rtol_mu=tol["mu"], rtol_sigma=tol["sigma"])
+    assert res.logs[-1]["collision_cost"] < res.logs[0]["collision_cost"]
+
+
+@pytest.mark.parametrize("prec,tol", [(FP64, TOL_FP64_SMALL), (MIXED, TOL_MIXED)])
+def test_point3d_block_form(pg, prec, tol):
+    pb, op = W.point3d(request=1, N=80)
+    res = gpu_solve([pb], [replace(op, plan_threads=64)], prec)[0]
+    compare_plan(pb, op, res, rtol_mu=tol["mu"], rtol_sigma=tol["sigma"])
+
+
+# ------------------------------------------------------- two-phase temperature
+
+@pytest.mark.parametrize("prec,tol,tpb", [(FP64, TOL_FP64_SMALL, 0), (MIXED, TOL_MIXED, 0), (MIXED_DF, TOL_MIXED, 0),
+                                          (FP64, TOL_FP64_SMALL, 64), (MIXED, TOL_MIXED, 64)])
+def test_two_phase_temperature(pg, prec, tol, tpb):
+    """T-hat = 1 for ten iterations, then 10 (the low/high schedule of the
+    planning experiments): the prior and the cost are rescaled at the switch."""
+    pb, op = W.c1_point2d(N=40, iters=20)
+    op = replace(op, temperature_high=10.0, switch_iter=10)
+    res = gpu_solve([pb], [replace(op, plan_threads=tpb)], prec)[0]
+    compare_plan(pb, op, res, rtol_mu=tol["mu"], rtol_sigma=tol["sigma"])
+    ent = [l["entropy"] for l in res.logs]
+    assert ent[-1] > ent[9] + 1.0                   # the high temperature favours entropy
+
+
+@pytest.mark.parametrize("tpb", [0, 64])
+def test_two_phase_temperature_slr(pg, tpb):
+    """The switch inside the second linearisation; later linearisations
+    rebuild the prior at the high temperature."""
+    pb, op = W.c4_quadrotor(N=40, iters=5, slr_iters=3)
+    op = replace(op, temperature_high=5.0, switch_iter=7)
+    res = gpu_solve([pb], [replace(op, plan_threads=tpb)], FP64)[0]
+    compare_plan(pb, op, res, rtol_mu=3e-8, rtol_sigma=1e-6)
+
+
+# ------------------------------------------------------- Smolyak sparse grids (Lemma 1)
+
+@pytest.mark.parametrize("prec,tol,tpb", [(FP64, TOL_FP64_SMALL, 0), (MIXED, TOL_MIXED, 0), (MIXED_DF, TOL_MIXED, 0),
+                                          (FP64, TOL_FP64_SMALL, 64)])
+def test_smolyak_point2d(pg, prec, tol, tpb):
+    """Level-3 sparse grid: the oracle integrates over all four dimensions,
+    the GPU over the two cost coordinates plus the level-2 trailing moments."""
+    pb, op = W.c1_point2d(N=40, iters=10)
+    op = replace(op, rule=W.RULE_SMOLYAK, gh_p=3)
+    res = gpu_solve([pb], [replace(op, plan_threads=tpb)], prec)[0]
+    compare_plan(pb, op, res, rtol_mu=tol["mu"], rtol_sigma=tol["sigma"])
+
+
+@pytest.mark.parametrize("k", [2, 3])
+@pytest.mark.parametrize("prec,tol", [(FP64, TOL_FP64_SMALL), (MIXED, TOL_MIXED)])
+def test_smolyak_arm(pg, k, prec, tol):
+    """The 7-DOF arm's cost depends on all seven joint angles: a level-k grid
+    over 7 dimensions (15 / 113 nodes) against the oracle's 14-dimensional grid."""
+    pb, op = W.c3_arm(N=24, iters=6)
+    op = replace(op, rule=W.RULE_SMOLYAK, gh_p=k)
+    res = gpu_solve([pb], [op], prec)[0]
+    compare_plan(pb, op, res, rtol_mu=tol["mu"], rtol_sigma=tol["sigma"])
+
+
+@pytest.mark.parametrize("tpb", [0, 64])
+def test_smolyak_quadrotor_slr(pg, tpb):
+    """SLR by a level-3 grid over the six state dimensions (85 nodes instead
+    of the 729 of the tensor rule)."""
+    pb, op = W.c4_quadrotor(N=40, iters=4, slr_iters=3)
+    op = replace(op, rule=W.RULE_SMOLYAK, gh_p=3)
+    res = gpu_solve([pb], [replace(op, plan_threads=tpb)], FP64)[0]
+    compare_plan(pb, op, res, rtol_mu=3e-8, rtol_sigma=1e-6)

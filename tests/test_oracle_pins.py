@@ -530,3 +530,89 @@ def test_monotone_total_cost_small_step(ora):
     tot = [l["prior_cost"] + l["collision_cost"] - l["entropy"] for l in st.logs]
     ups = sum(1 for a, b in zip(tot, tot[1:]) if b > a + 1e-9 * abs(a))
     assert ups <= 2, tot
+
+
+def test_two_phase_temperature_closed_form(ora):
+    """psi = 0, unbounded KL (beta = beta_max every iteration), Lambda_0 = K^-1
+    at T-hat = 1, then T-hat = 10 from iteration 5: the optimum at temperature
+    T is N(mu*, T K), so Lambda stays K^-1 for five iterations and then
+    contracts to K^-1 / 10 at rate 1/(beta+1):
+        Lambda_{5+m} = K^-1/10 + (beta+1)^-m (K^-1 - K^-1/10)."""
+    pb, op = W.c1_point2d(N=20, iters=40)
+    pb = replace(pb, cost_kind=W.COST_NONE)
+    op = replace(op, kl_eps=float("inf"), temperature_high=10.0, switch_iter=5)
+    st = ora.plan(pb, op)
+    pr = ora.prior(pb)
+    r = (1.0 + op.beta_max) ** -(op.iters - 5)
+    want_d = pr.Kd / 10.0 + r * (pr.Kd - pr.Kd / 10.0)
+    want_o = pr.Ko / 10.0 + r * (pr.Ko - pr.Ko / 10.0)
+    np.testing.assert_allclose(st.Ld, want_d, rtol=1e-9, atol=1e-9 * np.abs(pr.Kd).max())
+    np.testing.assert_allclose(st.Lo, want_o, rtol=1e-9, atol=1e-9 * np.abs(pr.Kd).max())
+    assert all(l["beta"] == op.beta_max for l in st.logs)
+    # the mean converges to the GP posterior mean, which does not depend on T-hat
+    assert np.linalg.norm(st.mu - pr.mubar) <= 1e-4 * np.linalg.norm(pr.mubar)
+    # entropy rises once the temperature is high (covariances grow towards 10 K)
+    assert st.logs[-1]["entropy"] > st.logs[4]["entropy"] + 0.5 * pb.n * (pb.N + 1) * np.log(5.0)
+
+
+# ------------------------------------------------------------ Smolyak sparse grids (Lemma 1)
+
+def _gauss_moment(a):
+    """E[prod xi_j^a_j] under N(0, I): prod (a_j - 1)!! for even a_j, else 0."""
+    out = 1.0
+    for m in a:
+        if m % 2:
+            return 0.0
+        out *= math.prod(range(m - 1, 0, -2)) if m > 1 else 1.0
+    return out
+
+
+@pytest.mark.parametrize("d,k", [(1, 4), (2, 2), (2, 3), (3, 3), (4, 4), (6, 3)])
+def test_smolyak_exact_to_total_degree(ora, d, k):
+    import itertools
+    xi, Wt = ora.rule(d, W.RULE_SMOLYAK, k)
+    assert abs(Wt.sum() - 1.0) < 1e-13
+    for deg in range(2 * k):
+        for alpha in itertools.combinations_with_replacement(range(d), deg):
+            a = np.bincount(alpha, minlength=d)
+            val = float(np.sum(Wt * np.prod(xi ** a, axis=1)))
+            assert abs(val - _gauss_moment(a)) < 1e-12 * max(1.0, _gauss_moment(a)), (a, val)
+    # not exact one degree higher: xi_0^(2k) has moment (2k-1)!!
+    a = np.zeros(d, dtype=int)
+    a[0] = 2 * k
+    assert abs(float(np.sum(Wt * xi[:, 0] ** (2 * k))) - _gauss_moment(a)) > 1e-3
+
+
+def test_smolyak_small_cases(ora):
+    """d = 1 is the k-point Gauss-Hermite rule; level 2 in d dims is the
+    origin (weight 1 - d) and +-e_j (1/2 each)."""
+    xi, Wt = ora.rule(1, W.RULE_SMOLYAK, 4)
+    x4, w4 = ora.gh_rule(4)
+    order = np.argsort(xi[:, 0])
+    np.testing.assert_allclose(xi[order, 0], np.sort(x4), atol=1e-14)
+    np.testing.assert_allclose(Wt[order], w4[np.argsort(x4)], atol=1e-14)
+    xi, Wt = ora.rule(3, W.RULE_SMOLYAK, 2)
+    assert len(Wt) == 7
+    k0 = np.where(np.all(xi == 0.0, axis=1))[0][0]
+    assert abs(Wt[k0] - (1 - 3)) < 1e-14
+    assert np.allclose(np.delete(Wt, k0), 0.5)
+
+
+@pytest.mark.parametrize("n,dc,k", [(4, 2, 3), (6, 3, 3), (14, 7, 2), (14, 7, 3)])
+def test_smolyak_reduces_to_the_cost_coordinates(ora, n, dc, k):
+    """For f depending on the leading dc coordinates, the n-dimensional grid
+    of level k gives the dc-dimensional grid's value, and a trailing second
+    moment xi_b^2 f gives the level k-1 value (what the reduced GPU
+    quadrature uses); odd trailing moments vanish."""
+    rng = np.random.default_rng(7)
+    c = rng.normal(size=dc)
+    f = lambda X: np.cos(X[:, :dc] @ c) + 0.3 * np.sin(X[:, 0]) ** 2
+    Xn, Wn = ora.rule(n, W.RULE_SMOLYAK, k)
+    Xd, Wd = ora.rule(dc, W.RULE_SMOLYAK, k)
+    Xe, We = ora.rule(dc, W.RULE_SMOLYAK, k - 1)
+    full = np.sum(Wn * f(Xn))
+    assert abs(full - np.sum(Wd * f(Xd))) < 1e-12
+    b = n - 1
+    assert abs(np.sum(Wn * Xn[:, b] ** 2 * f(Xn)) - np.sum(We * f(Xe))) < 1e-12
+    assert abs(np.sum(Wn * Xn[:, b] * f(Xn))) < 1e-12
+    assert abs(np.sum(Wn * Xn[:, b] * Xn[:, 0] * f(Xn))) < 1e-12

@@ -20,7 +20,7 @@ import numpy as np
 
 COST_NONE, COST_POINT2D, COST_POINT3D, COST_ARM, COST_QUADRATIC = 0, 1, 2, 3, 4
 DYN_LINEAR, DYN_PLANAR_QUAD, DYN_AFFINE_TEST = 0, 1, 2
-RULE_GH, RULE_DEG3 = 0, 1
+RULE_GH, RULE_DEG3, RULE_SMOLYAK = 0, 1, 2
 
 
 @dataclass
@@ -78,6 +78,8 @@ class Options:
     init_scale: float = 1.0
     replay_beta: Optional[np.ndarray] = None
     plan_threads: int = 0   # execution form of the CUDA path (0: thread per plan; 32..256: block per plan)
+    temperature_high: float = 0.0   # two-phase temperature: T-hat from switch_iter on (0: one phase)
+    switch_iter: int = 0
 
 
 def rng_for(config: int, request: int = 0) -> np.random.Generator:
@@ -300,6 +302,32 @@ def c3_arm(request: int = 0, N: int = 200, iters: int = 25, config: int = 3) -> 
     pb.dh, pb.sphere_link, pb.sphere_off, pb.sphere_r = dh, links, offs, radii
     pb.name = f"arm7_N{N}"
     op = Options(rule=RULE_DEG3, gh_p=3, beta_max=0.5, kl_eps=0.1 * (N + 1), max_bisect=10, iters=iters)
+    return pb, op
+
+
+def point3d(request: int = 0, N: int = 50, iters: int = 20, config: int = 6) -> Tuple[Problem, Options]:
+    """3-D point robot (the middle column of the paper's point-robot tables):
+    double integrator in 3-D (n=6), N=50 over T=5 s, Qc=0.8 I3, start
+    (0,0,0), goal (9,8,4), covariance 0.01 I6; 110x100x60 SDF at 0.1 m from
+    10 boxes (half-sides U(0.3,1.0)) kept clear of start and goal; eps=0.5,
+    sigma_obs=0.5; GH 3 points per dim (27 distinct points on the three
+    position coordinates); 20 iterations."""
+    rng = rng_for(config, request)
+    start, goal, eps = (0.0, 0.0, 0.0), (9.0, 8.0, 4.0), 0.5
+    pb = point_problem(3, N, 5.0, start, goal, 0.8, 0.01)
+    ends = np.array([start, goal])
+    boxes = []
+    while len(boxes) < 10:
+        c = np.array([rng.uniform(1.0, 9.0), rng.uniform(1.0, 8.0), rng.uniform(0.5, 4.5)])
+        h = rng.uniform(0.3, 1.0, size=3)
+        if np.all(_box_sdf(ends, c, h) > eps + 0.5):
+            boxes.append((c, h))
+    origin = (-1.0, -1.0, -1.0)
+    pb.sdf = sdf_grid_3d((110, 100, 60), origin, 0.1, boxes)
+    pb.sdf_origin, pb.sdf_cell = origin, 0.1
+    pb.cost_kind, pb.eps, pb.sigma_obs = COST_POINT3D, eps, 0.5
+    pb.name = f"point3d_N{N}"
+    op = Options(rule=RULE_GH, gh_p=3, beta_max=0.5, kl_eps=0.1 * (N + 1), max_bisect=10, iters=iters)
     return pb, op
 
 
