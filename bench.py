@@ -109,6 +109,15 @@ def fp32_peak_tflops():
 # (600*18 + 129*11 + 168*10) / (600*2 + 129 + 168) = 9.29.
 DF_EXPANSION = 9.29
 
+# DRAM bytes (read + write) per state per trial of the double-float fused
+# kernel (k_iterate<4, float, df64>, 128 registers), from one ncu capture of a
+# 2,368-plan, 2-iteration dense-horizon launch: 59.25 GB read + 23.60 GB
+# written over 52,096 trials x 751 states.  The algorithmic touch of one
+# state-trial (both sweeps re-read the five blocks, the scratch is written
+# and read back, the outputs written) is about 2.5 KB, so the kernel makes no
+# wasted re-reads.  A full launch's traffic is this times its state-trials.
+DF_DRAM_BYTES_PER_STATE_TRIAL = 82.85e9 / (52096 * 751)
+
 
 # --------------------------------------------------------------------- clocks
 
@@ -529,9 +538,14 @@ def main():
     for i in range(args.batch):
         r = bm.result(i, full=False)
         trials.append(sum(l["trials"] for l in r.logs))
+    state_trials = sum((pb.N + 1) * t for pb, t in zip(probs, trials))
     flops = algorithmic_fp64_flops(probs, trials)
     k_ms = min(it_ms)
+    traffic, traffic_note = None, "no capture of this form's kernel"
     if head == 2:
+        traffic = DF_DRAM_BYTES_PER_STATE_TRIAL * state_trials
+        traffic_note = ("bytes per launch: ncu dram bytes per state-trial of a 2,368-plan capture x this launch's "
+                        f"{state_trials} state-trials ({traffic / (k_ms / 1000.0) / 1e9:.0f} GB/s over the launch)")
         flops32 = flops * DF_EXPANSION
         achieved = flops32 / (k_ms / 1000.0) / 1e12
         peak = fp32_peak_tflops()
@@ -584,7 +598,8 @@ def main():
                        "note": "batch latency: every plan of a step completes at the end of the step"},
         **others,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                     "traffic": None, "kernel": kernel_name, "kernel_ms": k_ms, "peak_kind": roof_kind,
+                     "traffic": traffic, "traffic_note": traffic_note,
+                     "kernel": kernel_name, "kernel_ms": k_ms, "peak_kind": roof_kind,
                      "algorithmic_fp64_equivalent_flops": flops},
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": "plans/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
