@@ -10,6 +10,7 @@
 #include <functional>
 #include <map>
 #include <mutex>
+#include <set>
 #include <tuple>
 #include <string>
 #include <vector>
@@ -681,8 +682,10 @@ static pgvimp_status prepare(int count, const pgvimp_problem* problems, const pg
   if (count < 1 || !problems || !options) return fail(&B.err, PGVIMP_EINVAL, "count must be >= 1 with problems and options");
   if (precision != PGVIMP_PREC_PLAIN_FP64 && precision != PGVIMP_PREC_MIXED && precision != PGVIMP_PREC_MIXED_DF)
     return fail(&B.err, PGVIMP_EINVAL, "unknown precision");
+  std::set<const float*> scanned;   // a grid shared by several plans is scanned once
   for (int i = 0; i < count; ++i) {
-    pgvimp_status st = validate(problems[i], options[i], i, &B.err, scan_grids);
+    const bool scan = scan_grids && scanned.insert(problems[i].sdf).second;
+    pgvimp_status st = validate(problems[i], options[i], i, &B.err, scan);
     if (st != PGVIMP_OK) return st;
     if (problems[i].n != problems[0].n) return fail(&B.err, PGVIMP_EINVAL, "a batch needs one state dimension");
     if (problems[i].dyn_kind != problems[0].dyn_kind) return fail(&B.err, PGVIMP_EINVAL, "a batch needs one dynamics kind");
