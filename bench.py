@@ -129,7 +129,10 @@ class ClockSampler:
     def __init__(self, index: int):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+        # the raw samples go to PGVIMP_CLOCKS_DIR (default: the system temp directory)
+        import tempfile
+        out_dir = os.environ.get("PGVIMP_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(out_dir, f"pgvimp_clocks_rank{index}.csv")
 
     def __enter__(self):
         os.makedirs(os.path.dirname(self.path), exist_ok=True)
