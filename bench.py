@@ -601,6 +601,9 @@ def main():
                        "note": "batch latency: every plan of a step completes at the end of the step"},
         **others,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                     "fp64_equivalent": {"achieved": flops / (k_ms / 1000.0) / 1e12, "peak": fp64_peak_tflops(),
+                                         "frac": flops / (k_ms / 1000.0) / 1e12 / fp64_peak_tflops(),
+                                         "note": "the method's FP64 flops against the FP64 pipe's peak"},
                      "traffic": traffic, "traffic_note": traffic_note,
                      "kernel": kernel_name, "kernel_ms": k_ms, "peak_kind": roof_kind,
                      "algorithmic_fp64_equivalent_flops": flops},
