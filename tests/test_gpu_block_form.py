@@ -98,3 +98,27 @@ def test_block_form_batch_equals_alone(pg, prec):
         alone = gpu_solve([pbs[i]], [ops[i]], prec)[0]
         np.testing.assert_array_equal(together[i].mu, alone.mu)
         np.testing.assert_array_equal(together[i].Sd, alone.Sd)
+
+
+def test_c3_arm_full_size_block_form(pg):
+    """The arm at its full size (N = 200, 25 iterations) in the block form the server uses for it."""
+    pb, op = W.c3_arm()
+    res = gpu_solve([pb], [block(op, 256)], MIXED)[0]
+    compare_plan(pb, op, res, rtol_mu=TOL_MIXED["mu"], rtol_sigma=TOL_MIXED["sigma"])
+
+
+def test_c2_full_plan_invariants_block_form(pg):
+    """The whole 30-iteration N = 750 plan (chaotic in FP64, so checked by
+    invariants, as for the thread form)."""
+    pb, op = W.c2_point2d_dense()
+    res = gpu_solve([pb], [block(op, 256)], MIXED)[0]
+    assert len(res.logs) == op.iters
+    assert np.all(np.isfinite(res.mu)) and np.all(np.isfinite(res.Sd))
+    for S in res.Sd:
+        np.linalg.cholesky(0.5 * (S + S.T))
+    for l in res.logs:
+        if l["beta"] > 0:
+            assert l["kl"] <= op.kl_eps * (1 + 1e-12)
+            k = l["beta"] / op.beta_max * 2 ** op.max_bisect
+            assert abs(k - round(k)) < 1e-9
+    assert res.logs[-1]["collision_cost"] < res.logs[0]["collision_cost"]
