@@ -14,6 +14,14 @@
  * drift, by the SLR outer loop of Alg. 2 (Sec. 6.2).  Every step of that path
  * runs in this library's CUDA kernels; there is no CPU fallback.
  *
+ * Entry points: single plans (pgvimp_create / step / plan / get / destroy),
+ * batches of independent plans (pgvimp_batch_*), single rows of the path for
+ * inspection (pgvimp_batch_phase), a continuous-batching server
+ * (pgvimp_server_*), and an allocation-free marginals call.  Each plan runs
+ * in one of two execution forms chosen by pgvimp_options.plan_threads: one
+ * GPU thread per plan (throughput), or one thread block per plan with the
+ * block recursions by cyclic reduction over time (latency).
+ *
  * General rules for every entry point:
  *  - all functions are extern "C", never throw, never abort and return a
  *    pgvimp_status; on failure pgvimp_last_error() gives a one-line reason;
