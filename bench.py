@@ -217,7 +217,11 @@ def dist_init():
     if ws > 1:
         import torch
         import torch.distributed as dist
-        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)   # each rank's collectives on its own GPU
+            dist.init_process_group("nccl")
+        else:
+            dist.init_process_group("gloo")
     return ws, rank, local
 
 
