@@ -21,7 +21,7 @@ SOURCES = ["pgvimp_api.cu", "pgvimp_noalloc.cu", "pgvimp_server.cu"] + [f"k{n}_{
                                for part in ("iter_df", "iter_f32", "cta_f32", "iter_f64", "cta_f64",
                                             "aux", "aux_df", "rows")]
 HEADERS = ["pgvimp_device.cuh", "pgvimp_kernels.cuh", "pgvimp_cr.cuh", "pgvimp_plan.h", "pgvimp_launch.h",
-           "pgvimp_internal.h"]
+           "pgvimp_internal.h", "pgvimp_pool.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "-I", os.path.join(ROOT, "include")]
 
@@ -43,7 +43,7 @@ def _headers_of(src: str):
     elif src == "pgvimp_api.cu":
         base += ["pgvimp_device.cuh", "pgvimp_launch.h", "pgvimp_internal.h"]
     elif src == "pgvimp_server.cu":
-        base += ["pgvimp_internal.h"]
+        base += ["pgvimp_internal.h", "pgvimp_pool.h"]
     elif src == "pgvimp_noalloc.cu":
         base += ["pgvimp_device.cuh"]
     else:
