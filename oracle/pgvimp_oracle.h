@@ -15,10 +15,14 @@
  * Cross covariances follow the same rule: Soff[i] = Sigma_{i+1,i}.
  * The state is x = [q; qdot] with n = 2*nq for every robot model here.
  *
- * Parity status: every function is pinned by the CPU tests except the hinge/SDF
- * quadrature values and the arm cost, which are pinned only through invariants
- * and special cases (affine SDF, FK invariants); the paper prints no values for
- * them ("parity unpinned" beyond those).
+ * Parity status: every function is pinned by the CPU tests.  The hinge/SDF
+ * quadrature values, for which the paper prints no numbers, are pinned against
+ * independent integrals of the exact SDF of one disk (2-D, E[psi] and its
+ * first moment) and one sphere (3-D, E[psi]), besides the affine-SDF special
+ * case.  The arm cost is pinned by its planar special case (zero link twists
+ * and offsets: the textbook planar-arm formula over an affine SDF); the twist
+ * and offset terms of the DH chain only through invariants (rigid links, the
+ * base joint's rotation, the last joint's spin): "parity unpinned" beyond those.
  */
 #ifndef PGVIMP_ORACLE_H
 #define PGVIMP_ORACLE_H

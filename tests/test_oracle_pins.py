@@ -446,6 +446,88 @@ def test_hinge_inactive_gives_zero_and_factor_set(ora):
     assert abs(ora.psi(pb2, 2, np.zeros(4)) - 0.5 * 1.5 ** 2) < 1e-15
 
 
+def _polar_integral(f, rmax):
+    """Integral of f(x, y, rho) * rho over the disk of radius rmax around the
+    obstacle centre, in polar coordinates (scipy's adaptive quadrature)."""
+    from scipy import integrate
+    return integrate.dblquad(lambda rho, th: f(th, rho) * rho, 0.0, 2 * math.pi, 0.0, rmax,
+                             epsabs=1e-13, epsrel=1e-11)[0]
+
+
+def test_disk_hinge_moments_match_independent_integral(ora):
+    """Expected hinge cost of one disk obstacle (Sec. 4.2: E[psi] and E[psi (x - mu)]
+    over a factor's marginal) against an independent integral.
+
+    The hinge sigma * max(0, eps - sdf)^2 of a disk (centre c, radius r) is
+    supported on |p - c| < r + eps, so E[psi] and its first moment are
+    integrals of the exact disk SDF against the position marginal's density,
+    evaluated here by scipy in polar coordinates around c.  The oracle takes
+    the same expectations by its own route: a node-centred FP32 grid with
+    bilinear lookups, a 20-point-per-dimension Gauss-Hermite tensor rule over
+    all four state dimensions and sigma points from the lower Cholesky factor
+    of a correlated covariance.  The hinge is only C^1 at the band's edge, so
+    the rule converges slowly (0.3% at 12 points, 5e-5 at 20), and the 0.02 m
+    grid adds an interpolation error of about cell^2 / (8 |p - c|); 3e-3
+    covers both.  The obstacle and the mean sit off the diagonal, so a swapped
+    grid axis (61% off), a wrong hinge sign, weight form or origin fails."""
+    cx, cy, r, eps, sig = 1.3, 0.6, 0.9, 0.5, 0.7
+    org, cell = (-2.0, -2.5), 0.02
+    pb, op = W.c1_point2d(N=4)
+    grid = W.sdf_grid_2d(300, 300, org, cell, disks=[(cx, cy, r)])
+    pb = replace(pb, sdf=grid, sdf_origin=(org[0], org[1], 0.0), sdf_cell=cell, eps=eps, sigma_obs=sig)
+    mu = np.array([2.55, 0.95, 0.4, -0.3])
+    A = np.array([[0.30, 0.0, 0.0, 0.0], [0.12, 0.22, 0.0, 0.0], [0.05, -0.02, 0.3, 0.0], [0.01, 0.03, 0.04, 0.2]])
+    Sig = A @ A.T
+    P, m2 = Sig[:2, :2], mu[:2]
+    Pi, norm = np.linalg.inv(P), 1.0 / (2 * math.pi * math.sqrt(np.linalg.det(P)))
+
+    def weighted(k):
+        def f(th, rho):
+            d = np.array([cx + rho * math.cos(th), cy + rho * math.sin(th)]) - m2
+            w = sig * (r + eps - rho) ** 2 * norm * math.exp(-0.5 * d @ Pi @ d)
+            return w if k < 0 else w * d[k]
+        return f
+
+    E0 = _polar_integral(weighted(-1), r + eps)
+    E1 = np.array([_polar_integral(weighted(k), r + eps) for k in (0, 1)])
+    S0, S1, _ = ora.quad_moments(pb, replace(op, gh_p=20), 2, mu, Sig)
+    assert abs(S0 - E0) <= 3e-3 * E0, (S0, E0)
+    assert np.abs(S1[:2] - E1).max() <= 3e-3 * np.abs(E1).max(), (S1[:2], E1)
+
+
+def test_sphere_hinge_expectation_matches_independent_integral(ora):
+    """The trilinear 3-D path: E[psi] of one spherical obstacle for the 3-D point
+    robot (n = 6) against scipy's integral of the exact sphere SDF in
+    spherical coordinates around the centre.  The oracle runs a 10-point rule
+    on all six dimensions (10^6 points) over a 0.025 m FP32 grid stored
+    (z, y, x); it converges to 4e-5 here, and 2e-3 also covers the grid's
+    interpolation error.  Centre and mean differ in every coordinate, so a
+    permuted grid axis fails."""
+    from scipy import integrate
+    c, r, eps, sig = np.array([0.9, 0.5, 0.7]), 0.7, 0.4, 0.6
+    org, cell = (-1.0, -1.2, -0.9), 0.025
+    pb, op = W.point3d(N=4)
+    xs, ys, zs = (org[k] + cell * np.arange(m) for k, m in enumerate((140, 120, 110)))
+    Z, Y, X = np.meshgrid(zs, ys, xs, indexing="ij")
+    grid = (np.sqrt((X - c[0]) ** 2 + (Y - c[1]) ** 2 + (Z - c[2]) ** 2) - r).astype(np.float32)
+    pb = replace(pb, sdf=grid, sdf_origin=org, sdf_cell=cell, eps=eps, sigma_obs=sig)
+    mu = np.array([1.85, 0.95, 1.1, 0.2, -0.1, 0.3])
+    rng = np.random.default_rng(3)
+    A = np.tril(rng.uniform(-0.08, 0.08, (6, 6))) + np.diag([0.25, 0.2, 0.18, 0.2, 0.2, 0.2])
+    Sig = A @ A.T
+    P, m3 = Sig[:3, :3], mu[:3]
+    Pi, norm = np.linalg.inv(P), 1.0 / ((2 * math.pi) ** 1.5 * math.sqrt(np.linalg.det(P)))
+
+    def f(rho, th, ph):
+        u = np.array([math.sin(th) * math.cos(ph), math.sin(th) * math.sin(ph), math.cos(th)])
+        d = c + rho * u - m3
+        return sig * (r + eps - rho) ** 2 * norm * math.exp(-0.5 * d @ Pi @ d) * rho * rho * math.sin(th)
+
+    E0 = integrate.tplquad(f, 0.0, 2 * math.pi, 0.0, math.pi, 0.0, r + eps, epsabs=1e-11, epsrel=1e-8)[0]
+    S0, _, _ = ora.quad_moments(pb, replace(op, gh_p=10), 2, mu, Sig)
+    assert abs(S0 - E0) <= 2e-3 * E0, (S0, E0)
+
+
 def test_arm_fk_invariants(ora):
     pb, _ = W.c3_arm(N=10)
     rng = np.random.default_rng(0)
@@ -472,6 +554,54 @@ def test_arm_fk_invariants(ora):
         q3 = q.copy(); q3[6] += 1.1
         c3 = ora.arm_fk(pb, q3)
         np.testing.assert_allclose(c3[pb.sphere_link < 6], c[pb.sphere_link < 6], atol=1e-14)
+
+
+def test_planar_arm_cost_closed_form(ora):
+    """Arm cost psi = sum_s sigma * max(0, eps + r_s - sdf(c_s))^2 on a special
+    case with a textbook answer.  With every link twist, offset and joint
+    offset zero, the DH chain is a planar arm: link j starts at
+    P_j = sum_{k<j} l_k (cos th_k, sin th_k) with th_k = q_0 + ... + q_k, and a
+    sphere fixed at (u, v, w) in link j's frame sits at
+    P_j + u (cos th_j, sin th_j) + v (-sin th_j, cos th_j) + w e_z.  An affine
+    SDF a.p + d is reproduced exactly by trilinear interpolation, so psi has a
+    closed form up to the grid's FP32 rounding.  A wrong rotation order, a
+    translation applied before its rotation, a dropped radius or a hinge sign
+    fails it."""
+    pb, _ = W.c3_arm(N=4)
+    lengths = np.array([0.3, 0.25, 0.2, 0.15, 0.12, 0.1, 0.08])
+    dh = np.zeros((7, 4))
+    dh[:, 0] = lengths
+    rng = np.random.default_rng(11)
+    links = np.repeat(np.arange(7), 2).astype(np.int32)
+    offs = np.stack([rng.uniform(0.0, 1.0, 14) * lengths[links], rng.uniform(-0.05, 0.05, 14),
+                     rng.uniform(-0.05, 0.05, 14)], axis=1)
+    radii = rng.uniform(0.05, 0.12, 14)
+    a, d = np.array([0.6, -0.5, 0.3]), 0.25
+    org, cell, shape = (-1.5, -1.5, -0.3), 0.05, (13, 61, 61)      # (z, y, x) nodes
+    zs, ys, xs = (org[2 - k] + cell * np.arange(m) for k, m in enumerate(shape))
+    Z, Y, X = np.meshgrid(zs, ys, xs, indexing="ij")
+    grid = (a[0] * X + a[1] * Y + a[2] * Z + d).astype(np.float32)
+    eps, sig = 0.3, 3.0
+    pb = replace(pb, dh=dh, sphere_link=links, sphere_off=offs, sphere_r=radii, sdf=grid,
+                 sdf_origin=org, sdf_cell=cell, eps=eps, sigma_obs=sig)
+    active = []
+    for _ in range(6):
+        q = rng.uniform(-1.2, 1.2, 7)
+        th = np.cumsum(q)
+        P = np.concatenate([[[0.0, 0.0]], np.cumsum(lengths[:, None] * np.stack([np.cos(th), np.sin(th)], 1), 0)])
+        want = np.zeros((14, 3))
+        for k, j in enumerate(links):
+            u, v, w = offs[k]
+            want[k, :2] = P[j] + u * np.array([np.cos(th[j]), np.sin(th[j])]) + v * np.array([-np.sin(th[j]),
+                                                                                             np.cos(th[j])])
+            want[k, 2] = w
+        np.testing.assert_allclose(ora.arm_fk(pb, q), want, atol=1e-13)
+        h = np.maximum(0.0, eps + radii - (want @ a + d))
+        psi = sig * np.sum(h * h)
+        active.append(np.count_nonzero(h))
+        x = np.concatenate([q, rng.standard_normal(7)])
+        assert abs(ora.psi(pb, 2, x) - psi) <= 1e-5 * max(psi, 1e-3), (ora.psi(pb, 2, x), psi)
+    assert 0 < sum(active) < 6 * 14, active      # both sides of the hinge are exercised
 
 
 # ------------------------------------------------------------------------- SLR
