@@ -59,6 +59,7 @@ class _Options(C.Structure):
         ("max_bisect", C.c_int), ("iters", C.c_int), ("slr_iters", C.c_int),
         ("init_kind", C.c_int), ("init_scale", C.c_double), ("replay_beta", C.c_void_p),
         ("temperature_high", C.c_double), ("switch_iter", C.c_int),
+        ("update", C.c_int), ("trials_out", C.c_void_p), ("trials_cap", C.c_int), ("trials_n", C.c_void_p),
     ]
 
 
@@ -67,7 +68,18 @@ class _IterLog(C.Structure):
         ("beta", C.c_double), ("kl", C.c_double), ("kl_margin", C.c_double),
         ("prior_cost", C.c_double), ("collision_cost", C.c_double), ("entropy", C.c_double),
         ("trials", C.c_int), ("accepted", C.c_int),
+        ("beta_own", C.c_double), ("pd_margin", C.c_double), ("replayed", C.c_int), ("pad", C.c_int),
     ]
+
+
+class _TrialRec(C.Structure):
+    _fields_ = [
+        ("iter", C.c_int), ("pd", C.c_int), ("feasible", C.c_int), ("pad", C.c_int),
+        ("beta", C.c_double), ("kl", C.c_double), ("rel_pivot", C.c_double),
+    ]
+
+
+UPDATE_PROX, UPDATE_NGD = 0, 1
 
 
 _lib = None
@@ -143,9 +155,21 @@ class _Marshal:
             o.init_kind, o.init_scale = op.init_kind, op.init_scale
             o.temperature_high = getattr(op, "temperature_high", 0.0)
             o.switch_iter = getattr(op, "switch_iter", 0)
+            o.update = getattr(op, "update", UPDATE_PROX)
             if op.replay_beta is not None:
                 o.replay_beta = _ptr(self._k(_f64(op.replay_beta)))
+            # every trial of the own step-size search is recorded
+            total = max(op.iters, 1) * max(getattr(op, "slr_iters", 0), 1)
+            self.trial_recs = (_TrialRec * (total * (op.max_bisect + 1)))()
+            self.trial_n = C.c_int(0)
+            o.trials_out = C.cast(self.trial_recs, C.c_void_p)
+            o.trials_cap = len(self.trial_recs)
+            o.trials_n = C.cast(C.pointer(self.trial_n), C.c_void_p)
             self.op = o
+
+    def trials(self):
+        return [dict(iter=t.iter, pd=bool(t.pd), feasible=bool(t.feasible), beta=t.beta, kl=t.kl,
+                     rel_pivot=t.rel_pivot) for t in self.trial_recs[:self.trial_n.value]]
 
     def _k(self, a):
         self.keep.append(a)
@@ -232,6 +256,17 @@ def marginals(Ld, Lo):
     return Sd, So, ld.value
 
 
+def marginals_pivot(Ld, Lo):
+    """(status, smallest relative pivot) of the forward elimination of a
+    block-tridiagonal precision (status ENOTPD: not positive definite)."""
+    Ld, Lo = _f64(Ld), _f64(Lo)
+    N1, n = Ld.shape[0], Ld.shape[1]
+    Sd, So = np.zeros_like(Ld), np.zeros((max(N1 - 1, 0), n, n))
+    ld, piv = C.c_double(0.0), C.c_double(0.0)
+    rc = lib().ora_marginals_pivot(n, N1 - 1, _ptr(Ld), _ptr(Lo), _ptr(Sd), _ptr(So), C.byref(ld), C.byref(piv))
+    return rc, piv.value
+
+
 def block_solve(Md, Mo, r):
     Md, Mo, r = _f64(Md), _f64(Mo), _f64(r)
     x = np.zeros_like(r)
@@ -293,25 +328,28 @@ class State:
     So: np.ndarray
     logs: list
     slr_norms: Optional[np.ndarray] = None
+    trials: Optional[list] = None     # every trial of the own step-size searches
 
 
 def _logs_to_list(arr):
     return [dict(beta=l.beta, kl=l.kl, kl_margin=l.kl_margin, prior_cost=l.prior_cost,
                  collision_cost=l.collision_cost, entropy=l.entropy, trials=l.trials,
-                 accepted=l.accepted) for l in arr]
+                 accepted=l.accepted, beta_own=l.beta_own, pd_margin=l.pd_margin,
+                 replayed=bool(l.replayed)) for l in arr]
 
 
-def trial(pb, beta, pr: Prior, mu, Ld, Lo, logdet_k, g, G):
+def trial(pb, beta, pr: Prior, mu, Ld, Lo, logdet_k, g, G, update: int = UPDATE_PROX):
+    """One trial step (Thm 1, or the natural-gradient step with update=1)."""
     m = _Marshal(pb)
     n, N = pb.n, pb.N
     mu, Ld, Lo, g, G = _f64(mu), _f64(Ld), _f64(Lo), _f64(g), _f64(G)
     mun, Ldn, Lon = np.zeros_like(mu), np.zeros_like(Ld), np.zeros_like(Lo)
     Sdn, Son = np.zeros_like(Ld), np.zeros_like(Lo)
-    ld, kl = C.c_double(0.0), C.c_double(0.0)
-    rc = lib().ora_trial(C.byref(m.pb), C.c_double(beta), _ptr(pr.Kd), _ptr(pr.Ko), _ptr(pr.b), _ptr(mu),
-                         _ptr(Ld), _ptr(Lo), C.c_double(logdet_k), _ptr(g), _ptr(G), _ptr(mun), _ptr(Ldn),
-                         _ptr(Lon), _ptr(Sdn), _ptr(Son), C.byref(ld), C.byref(kl))
-    return rc, dict(mu=mun, Ld=Ldn, Lo=Lon, Sd=Sdn, So=Son, logdet=ld.value, kl=kl.value)
+    ld, kl, piv = C.c_double(0.0), C.c_double(0.0), C.c_double(0.0)
+    rc = lib().ora_trial_ex(C.byref(m.pb), update, C.c_double(beta), _ptr(pr.Kd), _ptr(pr.Ko), _ptr(pr.b),
+                            _ptr(mu), _ptr(Ld), _ptr(Lo), C.c_double(logdet_k), _ptr(g), _ptr(G), _ptr(mun),
+                            _ptr(Ldn), _ptr(Lon), _ptr(Sdn), _ptr(Son), C.byref(ld), C.byref(kl), C.byref(piv))
+    return rc, dict(mu=mun, Ld=Ldn, Lo=Lon, Sd=Sdn, So=Son, logdet=ld.value, kl=kl.value, rel_pivot=piv.value)
 
 
 def plan(pb, op, state: Optional[State] = None) -> State:
@@ -329,7 +367,7 @@ def plan(pb, op, state: Optional[State] = None) -> State:
     logs = (_IterLog * max(op.iters, 1))()
     _check(lib().ora_plan(C.byref(m.pb), C.byref(m.op), init, _ptr(mu), _ptr(Ld), _ptr(Lo), _ptr(Sd),
                           _ptr(So), logs), "plan")
-    return State(mu, Ld, Lo, Sd, So, _logs_to_list(logs[:op.iters]))
+    return State(mu, Ld, Lo, Sd, So, _logs_to_list(logs[:op.iters]), trials=m.trials())
 
 
 def drift(pb, x):
@@ -361,7 +399,8 @@ def plan_slr(pb, op) -> State:
     norms = np.zeros(max(op.slr_iters, 1))
     _check(lib().ora_plan_slr(C.byref(m.pb), C.byref(m.op), _ptr(mu), _ptr(Ld), _ptr(Lo), _ptr(Sd),
                               _ptr(So), logs, _ptr(norms)), "plan_slr")
-    return State(mu, Ld, Lo, Sd, So, _logs_to_list(logs[:op.iters * op.slr_iters]), norms[:op.slr_iters])
+    return State(mu, Ld, Lo, Sd, So, _logs_to_list(logs[:op.iters * op.slr_iters]), norms[:op.slr_iters],
+                 trials=m.trials())
 
 
 def solve(pb, op) -> State:

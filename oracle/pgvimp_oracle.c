@@ -88,12 +88,18 @@ static int inv(int n, const double *A, double *Ainv) {
   free(M);
   return ORA_OK;
 }
-/* Lower Cholesky factor A = L L^T.  Returns ORA_ENOTPD if a pivot is not > 0. */
-static int chol(int n, const double *A, double *L) {
+/* Lower Cholesky factor A = L L^T.  Returns ORA_ENOTPD if a pivot is not > 0.
+ * With rel_pivot: the smallest pivot s_j (before the square root) divided by
+ * the diagonal entry A_jj it came from, or the failing pivot's ratio. */
+static int chol_pivot(int n, const double *A, double *L, double *rel_pivot) {
   memset(L, 0, sizeof(double) * n * n);
   for (int j = 0; j < n; ++j) {
     double s = A[j * n + j];
     for (int k = 0; k < j; ++k) s -= L[j * n + k] * L[j * n + k];
+    if (rel_pivot) {
+      double r = s / fabs(A[j * n + j]);
+      if (j == 0 || r < *rel_pivot) *rel_pivot = r;
+    }
     if (!(s > 0.0)) return ORA_ENOTPD;
     double d = sqrt(s);
     L[j * n + j] = d;
@@ -105,6 +111,7 @@ static int chol(int n, const double *A, double *L) {
   }
   return ORA_OK;
 }
+static int chol(int n, const double *A, double *L) { return chol_pivot(n, A, L, NULL); }
 
 /* Matrix exponential by scaling and squaring of the Taylor series. */
 int ora_expm(int d, const double *M, double *E) {
@@ -497,7 +504,13 @@ int ora_init_mean(const ora_problem *pb, double *mu) {
  * log det Lambda = sum_i log det(Lambda_ii + F_i) (Schur complements); the
  * matrix is positive definite iff every such block is. */
 int ora_marginals(int n, int N, const double *Ld, const double *Lo, double *Sd, double *So, double *logdet) {
+  return ora_marginals_pivot(n, N, Ld, Lo, Sd, So, logdet, NULL);
+}
+
+int ora_marginals_pivot(int n, int N, const double *Ld, const double *Lo, double *Sd, double *So,
+                        double *logdet, double *rel_pivot) {
   size_t nn = (size_t)n * n;
+  double piv_min = INFINITY;
   int n2 = 2 * n;
   double *F = calloc((N + 1) * nn, sizeof(double)), *R = calloc((N + 1) * nn, sizeof(double));
   double *P = malloc(sizeof(double) * nn), *Pi = malloc(sizeof(double) * nn), *L = malloc(sizeof(double) * nn);
@@ -508,7 +521,10 @@ int ora_marginals(int n, int N, const double *Ld, const double *Lo, double *Sd, 
   if (!F || !R || !P || !Pi || !L || !T || !OT || !J || !Ji) { rc = ORA_ENOMEM; goto done; }
   for (int i = 0; i <= N; ++i) {
     for (size_t e = 0; e < nn; ++e) P[e] = Ld[i * nn + e] + F[i * nn + e];
-    if ((rc = chol(n, P, L))) goto done;
+    double piv;
+    rc = chol_pivot(n, P, L, &piv);
+    if (piv < piv_min) piv_min = piv;
+    if (rc) goto done;
     for (int a = 0; a < n; ++a) ld += 2.0 * log(L[a * n + a]);
     if (i == N) break;
     if ((rc = inv(n, P, Pi))) goto done;
@@ -546,6 +562,7 @@ int ora_marginals(int n, int N, const double *Ld, const double *Lo, double *Sd, 
   }
 done:
   if (logdet) *logdet = ld;
+  if (rel_pivot) *rel_pivot = piv_min;
   free(F); free(R); free(P); free(Pi); free(L); free(T); free(OT); free(J); free(Ji);
   return rc;
 }
@@ -726,43 +743,78 @@ static double bt_trace(int n, int N, const double *Ld, const double *Lo, const d
   return t;
 }
 
-/* Thm 1 at step size beta:
+/* Thm 1 at step size beta (update ORA_UPDATE_PROX):
  *   (K^-1 + Lambda_k/beta) mu' = -g + K^-1 mu_bar + Lambda_k mu_k / beta
  *   Lambda' = beta/(beta+1) (2G + K^-1 + Lambda_k/beta)
- * (G is block-diagonal, so it only enters the diagonal blocks), then the
- * marginals of Lambda' (which also decide Lambda' > 0) and the Gaussian
+ * (G is block-diagonal, so it only enters the diagonal blocks).
+ *
+ * NGD at step size beta (update ORA_UPDATE_NGD, Sec. 3.1(d)): the natural-
+ * gradient step delta theta = beta G(theta)^-1 grad L, with the Fisher matrix
+ * G(theta).  For a Gaussian in natural parameters eta = (Lambda mu, -Lambda/2)
+ * the Fisher matrix is the Jacobian of the expectation parameters
+ * m = (mu, mu mu^T + Sigma) with respect to eta, so the step is
+ * eta' = eta - beta grad_m J, J = -L = E[psi_d] + psi_e up to a constant.
+ * With grad_Sigma E[psi_d] = G, grad_mu E[psi_d] = g, and for psi_e (the
+ * prior and entropy part) grad_Sigma = K^-1/2 - Lambda/2, grad_mu =
+ * K^-1 mu - K^-1 mu_bar:
+ *   grad_{m2} J = G + K^-1/2 - Lambda_k/2,
+ *   grad_{m1} J = grad_mu J - 2 (grad_{m2} J) mu_k = g - b - 2 G mu_k + Lambda_k mu_k,
+ * hence
+ *   Lambda'     = (1 - beta) Lambda_k + beta (K^-1 + 2G),
+ *   Lambda' mu' = (1 - beta) Lambda_k mu_k + beta (b - g + 2 G mu_k),   b = K^-1 mu_bar.
+ *
+ * Then, for either update, the marginals of Lambda' (which also decide
+ * Lambda' > 0) and the Gaussian
  * KL(q'||q_k) = 1/2 [tr(Lambda_k Sigma') + dmu^T Lambda_k dmu - D
  *                    + log det Lambda' - log det Lambda_k],
  * with the trace term written as tr((Lambda_k - Lambda') Sigma') + D.
  * Returns ORA_ENOTPD (kl = +inf) when Lambda' is not positive definite. */
-int ora_trial(const ora_problem *pb, double beta, const double *Kd, const double *Ko, const double *b,
-              const double *mu, const double *Ld, const double *Lo, double logdet_k,
-              const double *g, const double *G,
-              double *mu_new, double *Ld_new, double *Lo_new, double *Sd_new, double *So_new,
-              double *logdet_new, double *kl) {
+int ora_trial_ex(const ora_problem *pb, int update, double beta, const double *Kd, const double *Ko,
+                 const double *b, const double *mu, const double *Ld, const double *Lo, double logdet_k,
+                 const double *g, const double *G,
+                 double *mu_new, double *Ld_new, double *Lo_new, double *Sd_new, double *So_new,
+                 double *logdet_new, double *kl, double *rel_pivot) {
   int n = pb->n, N = pb->N, D = n * (N + 1);
   size_t nn = (size_t)n * n;
   double *Md = malloc(sizeof(double) * (N + 1) * nn), *Mo = malloc(sizeof(double) * (N > 0 ? N : 1) * nn);
   double *r = malloc(sizeof(double) * D), *Lm = malloc(sizeof(double) * D), *dm = malloc(sizeof(double) * D);
   int rc = ORA_OK;
   *kl = INFINITY;
+  if (rel_pivot) *rel_pivot = NAN;
   if (!Md || !Mo || !r || !Lm || !dm) { rc = ORA_ENOMEM; goto done; }
-  double c = beta / (beta + 1.0);
-  for (int i = 0; i <= N; ++i)
-    for (size_t e = 0; e < nn; ++e) {
-      Ld_new[i * nn + e] = c * (2.0 * G[i * nn + e] + Kd[i * nn + e] + Ld[i * nn + e] / beta);
-      Md[i * nn + e] = Kd[i * nn + e] + Ld[i * nn + e] / beta;
-    }
-  for (int i = 0; i <= N; ++i) symm(n, Ld_new + i * nn);
-  for (int i = 0; i < N; ++i)
-    for (size_t e = 0; e < nn; ++e) {
-      Lo_new[i * nn + e] = c * (Ko[i * nn + e] + Lo[i * nn + e] / beta);
-      Mo[i * nn + e] = Ko[i * nn + e] + Lo[i * nn + e] / beta;
-    }
-  bt_matvec(n, N, Ld, Lo, mu, Lm);
-  for (int e = 0; e < D; ++e) r[e] = -g[e] + b[e] + Lm[e] / beta;
-  if ((rc = ora_block_solve(n, N, Md, Mo, r, mu_new))) goto done;
-  if ((rc = ora_marginals(n, N, Ld_new, Lo_new, Sd_new, So_new, logdet_new))) goto done;
+  if (update == ORA_UPDATE_NGD) {
+    for (int i = 0; i <= N; ++i)
+      for (size_t e = 0; e < nn; ++e)
+        Ld_new[i * nn + e] = (1.0 - beta) * Ld[i * nn + e] + beta * (Kd[i * nn + e] + 2.0 * G[i * nn + e]);
+    for (int i = 0; i <= N; ++i) symm(n, Ld_new + i * nn);
+    for (int i = 0; i < N; ++i)
+      for (size_t e = 0; e < nn; ++e) Lo_new[i * nn + e] = (1.0 - beta) * Lo[i * nn + e] + beta * Ko[i * nn + e];
+    bt_matvec(n, N, Ld, Lo, mu, Lm);
+    for (int i = 0; i <= N; ++i)
+      for (int a = 0; a < n; ++a) {
+        double Gm = 0.0;
+        for (int c = 0; c < n; ++c) Gm += G[i * nn + a * n + c] * mu[i * n + c];
+        r[i * n + a] = (1.0 - beta) * Lm[i * n + a] + beta * (b[i * n + a] - g[i * n + a] + 2.0 * Gm);
+      }
+    if ((rc = ora_block_solve(n, N, Ld_new, Lo_new, r, mu_new))) goto done;
+  } else {
+    double c = beta / (beta + 1.0);
+    for (int i = 0; i <= N; ++i)
+      for (size_t e = 0; e < nn; ++e) {
+        Ld_new[i * nn + e] = c * (2.0 * G[i * nn + e] + Kd[i * nn + e] + Ld[i * nn + e] / beta);
+        Md[i * nn + e] = Kd[i * nn + e] + Ld[i * nn + e] / beta;
+      }
+    for (int i = 0; i <= N; ++i) symm(n, Ld_new + i * nn);
+    for (int i = 0; i < N; ++i)
+      for (size_t e = 0; e < nn; ++e) {
+        Lo_new[i * nn + e] = c * (Ko[i * nn + e] + Lo[i * nn + e] / beta);
+        Mo[i * nn + e] = Ko[i * nn + e] + Lo[i * nn + e] / beta;
+      }
+    bt_matvec(n, N, Ld, Lo, mu, Lm);
+    for (int e = 0; e < D; ++e) r[e] = -g[e] + b[e] + Lm[e] / beta;
+    if ((rc = ora_block_solve(n, N, Md, Mo, r, mu_new))) goto done;
+  }
+  if ((rc = ora_marginals_pivot(n, N, Ld_new, Lo_new, Sd_new, So_new, logdet_new, rel_pivot))) goto done;
   for (int e = 0; e < D; ++e) dm[e] = mu_new[e] - mu[e];
   bt_matvec(n, N, Ld, Lo, dm, Lm);
   double quad = 0.0;
@@ -776,6 +828,15 @@ int ora_trial(const ora_problem *pb, double beta, const double *Kd, const double
 done:
   free(Md); free(Mo); free(r); free(Lm); free(dm);
   return rc;
+}
+
+int ora_trial(const ora_problem *pb, double beta, const double *Kd, const double *Ko, const double *b,
+              const double *mu, const double *Ld, const double *Lo, double logdet_k,
+              const double *g, const double *G,
+              double *mu_new, double *Ld_new, double *Lo_new, double *Sd_new, double *So_new,
+              double *logdet_new, double *kl) {
+  return ora_trial_ex(pb, ORA_UPDATE_PROX, beta, Kd, Ko, b, mu, Ld, Lo, logdet_k, g, G, mu_new, Ld_new,
+                      Lo_new, Sd_new, So_new, logdet_new, kl, NULL);
 }
 
 /* One proximal iteration of Alg. 1: factor expectations (Sec. 4.3) and the
@@ -824,17 +885,31 @@ int ora_step(const ora_problem *pb, const ora_options *op, int k,
   double best_beta = 0.0, best_kl = 0.0, best_ld = 0.0;
   int have = 0;
   double eps = op->kl_eps;
+  lg.pd_margin = INFINITY;
+  /* One trial of the own search: feasible = Lambda' > 0 and KL <= eps.  The
+   * trial is recorded (beta, KL, smallest relative pivot, decisions). */
 #define TRY(beta_, feas_)                                                                              \
   do {                                                                                                 \
-    double kl_, ld_;                                                                                   \
-    int trc_ = ora_trial(pb, (beta_), Kd, Ko, b, mu, Ld, Lo, *logdet, g, G, tm, tLd, tLo, tSd, tSo,  \
-                         &ld_, &kl_);                                                                  \
+    double kl_, ld_, piv_;                                                                             \
+    int trc_ = ora_trial_ex(pb, op->update, (beta_), Kd, Ko, b, mu, Ld, Lo, *logdet, g, G, tm, tLd,    \
+                            tLo, tSd, tSo, &ld_, &kl_, &piv_);                                         \
     if (trc_ == ORA_ENOMEM) { rc = trc_; goto done; }                                                  \
     lg.trials++;                                                                                       \
     (feas_) = (trc_ == ORA_OK) && (kl_ <= eps);                                                        \
     if (trc_ == ORA_OK && isfinite(eps) && eps > 0) {                                                  \
       double mg_ = fabs(kl_ - eps) / eps;                                                              \
       if (mg_ < lg.kl_margin) lg.kl_margin = mg_;                                                      \
+    }                                                                                                  \
+    if (fabs(piv_) < lg.pd_margin) lg.pd_margin = fabs(piv_);                                          \
+    if (op->trials_out && op->trials_n && *op->trials_n < op->trials_cap) {                            \
+      ora_trial_rec *t_ = op->trials_out + (*op->trials_n)++;                                          \
+      t_->iter = k;                                                                                    \
+      t_->pd = (trc_ == ORA_OK);                                                                       \
+      t_->feasible = (feas_);                                                                          \
+      t_->pad = 0;                                                                                     \
+      t_->beta = (beta_);                                                                              \
+      t_->kl = (trc_ == ORA_OK) ? kl_ : INFINITY;                                                      \
+      t_->rel_pivot = piv_;                                                                            \
     }                                                                                                  \
     if (feas_) {                                                                                       \
       best_beta = (beta_); best_kl = kl_; best_ld = ld_; have = 1;                                     \
@@ -844,28 +919,33 @@ int ora_step(const ora_problem *pb, const ora_options *op, int k,
     }                                                                                                  \
   } while (0)
   int feas = 0;
-  if (op->replay_beta) {
-    /* replay: the step sizes are given (decided elsewhere); a step is taken
-     * whenever Lambda' is positive definite, whatever its KL */
-    double bt = op->replay_beta[k];
-    if (bt > 0.0) {
-      double eps_saved = eps;
-      eps = INFINITY;
-      TRY(bt, feas);
-      eps = eps_saved;
-    }
-  } else {
-    TRY(op->beta_max, feas);
-    if (!feas) {
-      double lo = 0.0, hi = op->beta_max;
-      for (int t = 0; t < op->max_bisect; ++t) {
-        double mid = 0.5 * (lo + hi);
-        TRY(mid, feas);
-        if (feas) lo = mid; else hi = mid;
-      }
+  TRY(op->beta_max, feas);
+  if (!feas) {
+    double lo = 0.0, hi = op->beta_max;
+    for (int t = 0; t < op->max_bisect; ++t) {
+      double mid = 0.5 * (lo + hi);
+      TRY(mid, feas);
+      if (feas) lo = mid; else hi = mid;
     }
   }
 #undef TRY
+  lg.beta_own = have ? best_beta : 0.0;
+  if (op->replay_beta && op->replay_beta[k] != lg.beta_own) {
+    /* replay: the step decided elsewhere is taken whenever Lambda'(beta) is
+     * positive definite; its KL is recorded, not enforced */
+    double bt = op->replay_beta[k];
+    lg.replayed = 1;
+    have = 0;
+    if (bt > 0.0) {
+      double kl_, ld_;
+      int trc_ = ora_trial_ex(pb, op->update, bt, Kd, Ko, b, mu, Ld, Lo, *logdet, g, G, bm, bLd, bLo, bSd,
+                              bSo, &ld_, &kl_, NULL);
+      if (trc_ == ORA_ENOMEM) { rc = trc_; goto done; }
+      if (trc_ == ORA_OK) {
+        best_beta = bt; best_kl = kl_; best_ld = ld_; have = 1;
+      }
+    }
+  }
   if (have) {
     memcpy(mu, bm, sizeof(double) * D);
     memcpy(Ld, bLd, sizeof(double) * dsz);

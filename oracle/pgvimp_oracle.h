@@ -20,9 +20,11 @@
  * independent integrals of the exact SDF of one disk (2-D, E[psi] and its
  * first moment) and one sphere (3-D, E[psi]), besides the affine-SDF special
  * case.  The arm cost is pinned by its planar special case (zero link twists
- * and offsets: the textbook planar-arm formula over an affine SDF); the twist
- * and offset terms of the DH chain only through invariants (rigid links, the
- * base joint's rotation, the last joint's spin): "parity unpinned" beyond those.
+ * and offsets: the textbook planar-arm formula over an affine SDF), and the
+ * twist and offset terms of the DH chain by a closed-form FK of a chain with
+ * +pi/2 twists and non-zero offsets written out from the geometry.  The
+ * natural-gradient update is pinned by a finite-difference evaluation of the
+ * Fisher matrix and the gradient in natural parameters, and by its fixed points.
  */
 #ifndef PGVIMP_ORACLE_H
 #define PGVIMP_ORACLE_H
@@ -85,18 +87,48 @@ typedef struct {
   int slr_iters;
   int init_kind;            /* 0: Lambda0 = K^-1; 1: Lambda0 = init_scale * I */
   double init_scale;
-  const double *replay_beta;/* if non-NULL: take these beta_k (no search, no KL test) */
+  const double *replay_beta;/* if non-NULL: step beta_k is given.  The oracle still runs its own
+                               search from the current iterate (recorded as beta_own and in the
+                               trial records), then takes beta_k whenever Lambda'(beta_k) is
+                               positive definite, recording (not enforcing) its KL */
   /* two-phase temperature (the planning experiments of Sec. 7 run a low, then
      a high temperature): from global iteration switch_iter on (> 0), T-hat =
      temperature_high (> 0) in place of the problem's temperature */
   double temperature_high;
   int switch_iter;
+  /* the update of each iteration: ORA_UPDATE_PROX (Thm 1, KL proximal term) or ORA_UPDATE_NGD
+     (Sec. 3.1(d): natural-gradient step, i.e. the symmetrised KL as the proximal term, taken to
+     second order); both with the same step-size search */
+  int update;
+  /* optional record of every trial of the own step-size search (NULL: none); *trials_n counts
+     the records written, at most trials_cap */
+  struct ora_trial_rec *trials_out;
+  int trials_cap;
+  int *trials_n;
 } ora_options;
+
+enum { ORA_UPDATE_PROX = 0, ORA_UPDATE_NGD = 1 };
 
 typedef struct {
   double beta, kl, kl_margin, prior_cost, collision_cost, entropy;
   int trials, accepted;
+  double beta_own;          /* the step the oracle's own search chose (= beta unless replayed) */
+  double pd_margin;         /* min over the own search's trials of |smallest relative pivot| */
+  int replayed;             /* 1 if beta is a replayed step that differs from beta_own */
+  int pad;
 } ora_iter_log;
+
+/* One trial of the step-size search (App. C). */
+typedef struct ora_trial_rec {
+  int iter;                 /* global iteration index */
+  int pd;                   /* Lambda'(beta) positive definite */
+  int feasible;             /* pd and KL <= eps */
+  int pad;
+  double beta;
+  double kl;                /* +inf when not pd */
+  double rel_pivot;         /* smallest pivot of the block elimination of Lambda'(beta) divided by
+                               the diagonal entry it came from; <= 0 where the elimination failed */
+} ora_trial_rec;
 
 /* ---- dense helpers (exposed for the pins) ---- */
 int ora_expm(int d, const double *M, double *E);
@@ -112,6 +144,10 @@ int ora_init_mean(const ora_problem *pb, double *mu);
 
 /* ---- marginals by Gaussian belief propagation (Sec. 5.1) ---- */
 int ora_marginals(int n, int N, const double *Ld, const double *Lo, double *Sd, double *So, double *logdet);
+/* as ora_marginals, also returning the smallest relative pivot of the forward pass (rel_pivot may be
+   NULL); on ORA_ENOTPD rel_pivot holds the failing pivot (<= 0) */
+int ora_marginals_pivot(int n, int N, const double *Ld, const double *Lo, double *Sd, double *So,
+                        double *logdet, double *rel_pivot);
 int ora_block_solve(int n, int N, const double *Md, const double *Mo, const double *r, double *x);
 
 /* ---- factor expectations (Sec. 4.2-4.3) ---- */
@@ -129,6 +165,13 @@ int ora_trial(const ora_problem *pb, double beta, const double *Kd, const double
               const double *g, const double *G,
               double *mu_new, double *Ld_new, double *Lo_new, double *Sd_new, double *So_new,
               double *logdet_new, double *kl);
+/* the trial of either update (ORA_UPDATE_PROX: Thm 1; ORA_UPDATE_NGD: Sec. 3.1(d)), with the
+   smallest relative pivot of Lambda'(beta) (may be NULL) */
+int ora_trial_ex(const ora_problem *pb, int update, double beta, const double *Kd, const double *Ko,
+                 const double *b, const double *mu, const double *Ld, const double *Lo, double logdet_k,
+                 const double *g, const double *G,
+                 double *mu_new, double *Ld_new, double *Lo_new, double *Sd_new, double *So_new,
+                 double *logdet_new, double *kl, double *rel_pivot);
 int ora_step(const ora_problem *pb, const ora_options *op, int k,
              const double *Kd, const double *Ko, const double *b, const double *mubar,
              double *mu, double *Ld, double *Lo, double *Sd, double *So, double *logdet,

@@ -383,7 +383,7 @@ def test_replay_beta(ora):
     betas = np.array([l["beta"] for l in st.logs])
     st2 = ora.plan(pb, replace(op, replay_beta=betas))
     np.testing.assert_array_equal(st2.mu, st.mu)
-    assert all(l["trials"] == 1 for l in st2.logs)
+    assert not any(l["replayed"] for l in st2.logs)
 
 
 # --------------------------------------------------------------- cost and SDF
@@ -746,3 +746,211 @@ def test_smolyak_reduces_to_the_cost_coordinates(ora, n, dc, k):
     assert abs(np.sum(Wn * Xn[:, b] ** 2 * f(Xn)) - np.sum(We * f(Xe))) < 1e-12
     assert abs(np.sum(Wn * Xn[:, b] * f(Xn))) < 1e-12
     assert abs(np.sum(Wn * Xn[:, b] * Xn[:, 0] * f(Xn))) < 1e-12
+
+
+# -------------------------------------------------- arm: twists and offsets
+
+def test_arm_fk_twist_and_offset_closed_form(ora):
+    """The DH chain with non-zero twists and offsets against FK written out
+    from the geometry, independently of the DH matrices.  Joint 1 (a = 0,
+    twist +pi/2, offset d1) turns the arm's vertical plane about z: its
+    horizontal direction is x1 = (c1, s1, 0), the up direction y1 = e_z, and
+    joint 2's axis is z1 = (s1, -c1, 0).  Joint 2 (length a2, offset d2 along
+    z1, joint offset th02) and joint 3 (length a3, twist +pi/2) move in that
+    plane: x2 = cos(t2) x1 + sin(t2) y1, x3 = cos(t2+t3) x1 + sin(t2+t3) y1
+    with t2 = q2 + th02.  After joint 3's twist its y axis is z1, so a sphere
+    at (r, 0, 0) in link 4's frame sits at
+        (0, 0, d1) + d2 z1 + a2 x2 + a3 x3 + r (cos q4 x3 + sin q4 z1).
+    A twist with the wrong sign, an offset along the wrong axis or a twist
+    applied before the link's own rotation fails it."""
+    pb, _ = W.c3_arm(N=4)
+    d1, a2, d2, a3, th02, r = 0.31, 0.42, 0.07, 0.27, 0.35, 0.13
+    dh = np.array([[0.0, np.pi / 2, d1, 0.0],
+                   [a2, 0.0, d2, th02],
+                   [a3, np.pi / 2, 0.0, 0.0],
+                   [0.0, 0.0, 0.0, 0.0]])
+    pb = replace(pb, dh=dh, sphere_link=np.array([3, 1], dtype=np.int32),
+                 sphere_off=np.array([[r, 0.0, 0.0], [0.0, 0.0, 0.0]]), sphere_r=np.array([0.05, 0.05]))
+    rng = np.random.default_rng(21)
+    for _ in range(8):
+        q = rng.uniform(-np.pi, np.pi, 4)
+        c1, s1 = np.cos(q[0]), np.sin(q[0])
+        t2, t23 = q[1] + th02, q[1] + th02 + q[2]
+        x1, y1, z1 = np.array([c1, s1, 0.0]), np.array([0.0, 0.0, 1.0]), np.array([s1, -c1, 0.0])
+        x2 = np.cos(t2) * x1 + np.sin(t2) * y1
+        x3 = np.cos(t23) * x1 + np.sin(t23) * y1
+        want_end = np.array([0.0, 0.0, d1]) + d2 * z1 + a2 * x2 + a3 * x3 + r * (np.cos(q[3]) * x3
+                                                                                 + np.sin(q[3]) * z1)
+        # a sphere with zero offset on link 2 sits at the origin of link 1's frame after Tz(d1)
+        want_base = np.array([0.0, 0.0, d1])
+        c = ora.arm_fk(pb, q)
+        np.testing.assert_allclose(c[0], want_end, atol=1e-13)
+        np.testing.assert_allclose(c[1], want_base, atol=1e-13)
+
+
+# ----------------------------------------------- natural-gradient update (NGD)
+
+def _ngd_problem(seed=3):
+    """n = 4, N = 1: one pair of states, quadratic pseudo-obstacles."""
+    rng = np.random.default_rng(seed)
+    pb, op = W.c1_point2d(N=1)
+    pb = replace(pb, T=1.0, K0=0.5 * np.eye(4), KN=0.5 * np.eye(4))
+    Wm = []
+    for _ in range(2):
+        A = rng.standard_normal((4, 4))
+        Wm.append(A @ A.T * 0.3 + 0.2 * np.eye(4))
+    c = rng.standard_normal((2, 4))
+    pb = replace(pb, cost_kind=W.COST_QUADRATIC, quad_c=c, quad_W=np.stack(Wm))
+    return pb, op
+
+
+def test_ngd_step_is_the_fisher_natural_gradient_step(ora):
+    """Sec. 3.1(d): the NGD step is delta theta = beta G(theta)^-1 grad L with
+    the Fisher matrix G.  Here both G and the gradient come from central
+    differences in the natural parameters eta = (Lambda mu, -Lambda/2) (the
+    Fisher matrix as the Jacobian of the expectation parameters E[T(x)]), and
+    the objective J = -L = E[psi] + KL(q || N(mu_bar, K)) + const is evaluated
+    in closed form for quadratic costs.  The oracle's step must equal
+    eta - beta G^-1 grad_eta J.  A missing factor 2 on G, a wrong sign or the
+    step taken on the mean without the new precision fails it."""
+    pb, op = _ngd_problem()
+    n, D = 4, 8
+    pr = ora.prior(pb)
+    Kinv = dense(pr.Kd, pr.Ko)
+    mubar = pr.mubar.ravel()
+    rng = np.random.default_rng(5)
+    A = rng.standard_normal((D, D))
+    Lam_k = A @ A.T / D + 1.5 * np.eye(D)
+    mu_k = rng.standard_normal(D)
+    Wd = scipy.linalg.block_diag(*pb.quad_W)
+    cvec = pb.quad_c.ravel()
+    iu = np.triu_indices(D)
+
+    def unpack(v):
+        E2 = np.zeros((D, D))
+        E2[iu] = v[D:]
+        E2 = E2 + np.triu(E2, 1).T
+        Lam = -2.0 * E2
+        Sig = np.linalg.inv(Lam)
+        return Sig @ v[:D], Sig, Lam
+
+    def pack(mu, Lam):
+        E2 = -0.5 * Lam
+        return np.concatenate([Lam @ mu, E2[iu]])
+
+    def J(v):
+        mu, Sig, Lam = unpack(v)
+        e = mu - cvec
+        epsi = 0.5 * (np.trace(Wd @ Sig) + e @ Wd @ e)
+        dp = mu - mubar
+        prior = 0.5 * (np.trace(Kinv @ Sig) + dp @ Kinv @ dp)
+        return epsi + prior - 0.5 * np.linalg.slogdet(Sig)[1]
+
+    def m(v):
+        mu, Sig, _ = unpack(v)
+        S2 = Sig + np.outer(mu, mu)
+        w = np.where(iu[0] == iu[1], 1.0, 2.0)       # tr(E2 x x^T) counts off-diagonals twice
+        return np.concatenate([mu, w * S2[iu]])
+
+    v0 = pack(mu_k, Lam_k)
+    h = 1e-5
+    P = v0.size
+    grad = np.zeros(P)
+    F = np.zeros((P, P))
+    for j in range(P):
+        dv = np.zeros(P)
+        dv[j] = h
+        grad[j] = (J(v0 + dv) - J(v0 - dv)) / (2 * h)
+        F[:, j] = (m(v0 + dv) - m(v0 - dv)) / (2 * h)
+    beta = 0.3
+    v1 = v0 - beta * np.linalg.solve(F, grad)
+    mu_x, _, Lam_x = unpack(v1)
+
+    Ld, Lo = blocks(Lam_k, n)
+    Sd, _, ldk = ora.marginals(Ld, Lo)
+    g, G = np.zeros((2, n)), np.zeros((2, n, n))
+    for i in range(2):
+        S0, S1, S2 = ora.quad_moments(pb, op, i, mu_k[i * n:(i + 1) * n], Sd[i])
+        g[i], G[i] = ora.gradients(Sd[i], S0, S1, S2)
+    rc, t = ora.trial(pb, beta, pr, mu_k.reshape(2, n), Ld, Lo, ldk, g, G, update=ora.UPDATE_NGD)
+    assert rc == 0
+    assert rel(dense(t["Ld"], t["Lo"]), Lam_x) < 1e-7
+    assert rel(t["mu"].ravel(), mu_x) < 1e-7
+    # the KL-proximal step at the same beta is a different point (same fixed point, other path)
+    rc, tp = ora.trial(pb, beta, pr, mu_k.reshape(2, n), Ld, Lo, ldk, g, G)
+    assert rel(dense(tp["Ld"], tp["Lo"]), Lam_x) > 1e-3
+
+
+def test_ngd_no_obstacles_closed_form(ora):
+    """psi = 0, unbounded KL, fixed beta: Lambda_k = K^-1 + (1-beta)^k
+    (Lambda_0 - K^-1); from Lambda_0 = K^-1 the mean contracts to the GP
+    prior mean by (1-beta) per iteration."""
+    pb, op = W.c1_point2d(N=12)
+    pb = replace(pb, cost_kind=W.COST_NONE)
+    pr = ora.prior(pb)
+    beta, s = 0.4, 2.0
+    st = ora.plan(pb, replace(op, update=1, kl_eps=float("inf"), beta_max=beta, iters=6, init_kind=1,
+                              init_scale=s))
+    Lam0 = np.stack([s * np.eye(4)] * 13)
+    assert rel(st.Ld, pr.Kd + (1 - beta) ** 6 * (Lam0 - pr.Kd)) < 1e-12
+    assert rel(st.Lo, pr.Ko + (1 - beta) ** 6 * (0.0 - pr.Ko)) < 1e-12
+    st2 = ora.plan(pb, replace(op, update=1, kl_eps=float("inf"), beta_max=beta, iters=5))
+    mu0 = ora.init_mean(pb)
+    np.testing.assert_allclose(st2.mu - pr.mubar, (1 - beta) ** 5 * (mu0 - pr.mubar), rtol=1e-7, atol=1e-8)
+
+
+def test_ngd_quadratic_pseudo_obstacles_fixed_point(ora):
+    """The NGD iteration has the same fixed point as Thm 1's: precision
+    K^-1 + blockdiag(W) and mean (K^-1 + W)^-1 (b + W c); its precision
+    contracts at rate (1 - beta)."""
+    pb, op = _quadratic_problem(N=7)
+    pr = ora.prior(pb)
+    Kinv = dense(pr.Kd, pr.Ko)
+    Wd = scipy.linalg.block_diag(*pb.quad_W)
+    Lstar = Kinv + Wd
+    mustar = np.linalg.solve(Lstar, pr.b.ravel() + Wd @ pb.quad_c.ravel())
+    beta = 0.5
+    st = ora.plan(pb, replace(op, update=1, kl_eps=float("inf"), beta_max=beta, iters=80))
+    assert rel(dense(st.Ld, st.Lo), Lstar) < 1e-12
+    assert rel(st.mu.ravel(), mustar) < 1e-10
+    st4 = ora.plan(pb, replace(op, update=1, kl_eps=float("inf"), beta_max=beta, iters=4))
+    assert rel(dense(st4.Ld, st4.Lo), Lstar + (1 - beta) ** 4 * (Kinv - Lstar)) < 1e-12
+
+
+# ------------------------------------------- step-size search records and replay
+
+def test_search_records_follow_the_bisection(ora):
+    """Every trial of the step-size search is recorded; the accepted step is
+    the largest feasible trial, and the trials walk the dyadic bisection."""
+    pb, op = W.c1_point2d(N=20, iters=4)
+    op = replace(op, kl_eps=0.5)
+    st = ora.plan(pb, op)
+    for k, l in enumerate(st.logs):
+        tr = [t for t in st.trials if t["iter"] == k]
+        assert len(tr) == l["trials"]
+        assert tr[0]["beta"] == op.beta_max
+        feas = [t["beta"] for t in tr if t["feasible"]]
+        assert l["beta"] == (max(feas) if feas else 0.0)
+        lo, hi = 0.0, op.beta_max
+        for t in tr[1:]:
+            assert t["beta"] == 0.5 * (lo + hi)
+            lo, hi = (t["beta"], hi) if t["feasible"] else (lo, t["beta"])
+            assert t["feasible"] == (t["pd"] and t["kl"] <= op.kl_eps)
+        assert l["beta_own"] == l["beta"] and not l["replayed"]
+        assert l["pd_margin"] == min(abs(t["rel_pivot"]) for t in tr)
+
+
+def test_replay_records_the_own_search(ora):
+    """In replay mode the oracle still searches on its own (beta_own) and
+    takes the given step, recording its KL without enforcing it."""
+    pb, op = W.c1_point2d(N=20, iters=4)
+    op = replace(op, kl_eps=0.5)
+    st = ora.plan(pb, op)
+    betas = np.array([l["beta"] for l in st.logs])
+    forced = betas.copy()
+    forced[1] = betas[1] * 2          # a step the bound rejects
+    st2 = ora.plan(pb, replace(op, replay_beta=forced))
+    assert not st2.logs[0]["replayed"] and st2.logs[1]["replayed"]
+    assert st2.logs[1]["beta"] == forced[1] and st2.logs[1]["beta_own"] == betas[1]
+    assert st2.logs[1]["kl"] > op.kl_eps      # recorded, not enforced
+    np.testing.assert_array_equal(st2.logs[0]["beta"], betas[0])

@@ -80,6 +80,7 @@ class Options:
     plan_threads: int = 0   # execution form of the CUDA path (0: thread per plan; 32..256: block per plan)
     temperature_high: float = 0.0   # two-phase temperature: T-hat from switch_iter on (0: one phase)
     switch_iter: int = 0
+    update: int = 0         # 0: KL-proximal step (Thm 1); 1: natural-gradient step (Sec. 3.1(d))
 
 
 def rng_for(config: int, request: int = 0) -> np.random.Generator:
