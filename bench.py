@@ -331,6 +331,7 @@ def run_served(mix, precision, plan_threads, max_inflight=32, max_batch=16, wind
             "makespan_s": span_s, "requests": len(mix), "batches": st["batches"] - len(seen),
             "mean_batch": sum(sizes) / len(sizes), "submit_lag_ms_max": 1000.0 * max(lags),
             "host_launch_ms": st["host_launch_ms"], "host_collect_ms": st["host_collect_ms"],
+            "graph_launches": st["graph_launches"], "graph_instantiations": st["graph_instantiations"],
             "precision": precision, "plan_threads": plan_threads, "max_inflight": max_inflight,
             "max_batch": max_batch, "batch_window_ms": window_ms}
 
@@ -389,11 +390,78 @@ def serving(args):
     # served FP32/FP64: FP32 quadrature, FP64 recursions, block form, continuous batching
     out["autotune"] = {"seconds": tune_s, "table": {f"n{k[0]}/dyn{k[1]}/log2N{k[2]}": v for k, v in tuner.table.items()}}
     out["served_fp32_fp64"] = run_served(mix, 1, -1)
+    out["served_fp32_double_float"] = run_served(mix, 2, -1)
     out["served_plain_fp64"] = run_served(mix, 0, -1)
     sample = mix[:args.plain_count]
     out["plain_sample"] = f"first {len(sample)} requests of the mix (arrival times kept)"
     out["plain_fp64_per_request"] = run_plain(sample)
     out["served_fp32_fp64_on_sample"] = run_served(sample, 1, -1)
+    return out
+
+
+# ---------------------------------------------------- the other configurations
+
+def other_configs(args):
+    """Batch throughput of the other workloads in their throughput form, the
+    single-plan latency of every workload in the block (latency) form, and the
+    roofline fraction of each batch's fused kernel.  One timed run each, after
+    one untimed run; CUDA events on the launching stream."""
+    from dataclasses import replace
+
+    import torch
+
+    import workloads as W
+    from paper_2411_03416_b300 import _lib as L
+    st = torch.cuda.Stream()
+    sh = st.cuda_stream
+
+    def timed(probs, opts, prec):
+        b = L.Batch(probs, opts, prec)
+        b.upload(sh)
+        for k in range(2):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            b.reset(sh)
+            e0.record(st)
+            b.run(0, sh)
+            e1.record(st)
+            torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        b.download_results(sh)
+        torch.cuda.synchronize()
+        trials = [sum(l["trials"] for l in b.result(i, full=False).logs) for i in range(len(probs))]
+        b.close()
+        return ms, trials
+
+    cfgs = {
+        "C1 point robot, N=50, GH 3, 20 iterations": (lambda r: W.c1_point2d(request=r), 75776, 4, 2),
+        "C3 7-DOF arm, N=200, degree-3 rule, 25 iterations": (lambda r: W.c3_arm(request=r), 4736, 7, 2),
+        "C4 planar quadrotor SLR, N=300, 10 x 15 iterations": (lambda r: W.c4_quadrotor(request=r), 4736, 2, 2),
+    }
+    out = {}
+    for name, (make, count, dc, prec) in cfgs.items():
+        base = [make(r) for r in range(8)]
+        probs = [base[i % 8][0] for i in range(count)]
+        opts = [base[i % 8][1] for i in range(count)]
+        ms, trials = timed(probs, opts, prec)
+        pb0, op0 = base[0]
+        iters = op0.iters * max(op0.slr_iters, 1) if pb0.dyn_kind else op0.iters
+        n = pb0.n
+        flops = sum((pb.N + 1) * (t * fp64_flops_per_trial_state(n) + iters * fp64_flops_per_iter_state(n, dc))
+                    for pb, t in zip(probs, trials))
+        ach = flops * DF_EXPANSION / (ms / 1000.0) / 1e12
+        form = "lane form (16 lanes per plan)" if n == 4 else "thread form (one thread per plan)"
+        entry = {"batch": count, "form": form, "precision": DTYPES[prec], "ms": ms, "plans_per_s": count / (ms / 1000.0),
+                 "roofline": {"bound": "alu", "achieved": ach, "peak": fp32_peak_tflops(), "unit": "TFLOP/s",
+                              "frac": ach / fp32_peak_tflops(),
+                              "note": "FP64-equivalent flops of the trials and updates x 9.29 FP32 flops each; "
+                                      "the SLR linearisation and prior rebuilds are not counted"}}
+        lat = {}
+        for prec_l in (1, 2):
+            lpb, lop = base[0]
+            ms_l, _ = timed([lpb], [replace(lop, plan_threads=256)], prec_l)
+            lat[DTYPES[prec_l]] = ms_l
+        entry["single_plan_latency_ms_block_form_256"] = lat
+        out[name] = entry
     return out
 
 
@@ -410,7 +478,11 @@ def kernel_only(args):
 
     from paper_2411_03416_b300 import _lib as L
     probs, opts = make_batch_problems(args.batch)
-    opts = [replace(o, iters=args.iters, plan_threads=args.plan_threads) for o in opts]
+    if args.kernel_n:
+        # a shorter horizon of the same plans (a profiling case that fits a few GB at full occupancy)
+        probs = [replace(p, N=args.kernel_n, T=p.T * args.kernel_n / p.N) for p in probs]
+    opts = [replace(o, iters=args.iters, plan_threads=args.plan_threads,
+                    kl_eps=0.1 * (probs[0].N + 1) if args.kernel_n else o.kl_eps) for o in opts]
     b = L.Batch(probs, opts, PRECISIONS[args.precision])
     st = torch.cuda.Stream()
     sh = st.cuda_stream
@@ -428,7 +500,7 @@ def kernel_only(args):
     trials = [sum(l["trials"] for l in b.result(i, full=False).logs) for i in range(args.batch)]
     ms = e0.elapsed_time(e1)
     flops = algorithmic_fp64_flops(probs, trials, args.iters)
-    print(f"kernel-only: batch {args.batch}, {args.iters} iterations, {args.precision}, "
+    print(f"kernel-only: batch {args.batch}, N {probs[0].N}, {args.iters} iterations, {args.precision}, "
           f"plan_threads {args.plan_threads}: {ms:.1f} ms, "
           f"{sum(trials)} trials, {flops / ms / 1e9:.4f} TFLOP/s-equivalent", flush=True)
     b.close()
@@ -452,10 +524,12 @@ def main():
     ap.add_argument("--kernel-only", action="store_true",
                     help="profiling target: prior phase, then one fused-iteration launch; no JSON line")
     ap.add_argument("--iters", type=int, default=ITERS, help="proximal iterations (kernel-only mode)")
+    ap.add_argument("--kernel-n", type=int, default=0, help="kernel-only mode: horizon N (0: the workload's 750)")
     ap.add_argument("--plan-threads", type=int, default=0,
-                    help="kernel-only mode: 0 thread form, 32..256 block form (threads per plan)")
+                    help="kernel-only mode: 0 default form, 1 thread form, 16 lane form, 32..256 block form")
     ap.add_argument("--serve-count", type=int, default=512, help="requests of the serving mix (0: skip serving)")
     ap.add_argument("--plain-count", type=int, default=32, help="requests of the plain per-request FP64 sample")
+    ap.add_argument("--no-configs", action="store_true", help="skip the other configurations' batch and latency runs")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -589,6 +663,7 @@ def main():
             others["served_double_float_recursions"] = time_steps(L.PREC_MIXED_DF, args.plain_steps)
 
     serve = serving(args) if (args.serve_count > 0 and rank == 0) else None
+    configs = other_configs(args) if (rank == 0 and not args.no_configs) else None
 
     if rank != 0:
         return
@@ -614,6 +689,7 @@ def main():
         "e2e": {"value": e2e_value, "unit": "plans/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "ms_per_step": statistics.median(e2e_ms)},
         "serving": serve,
+        "configs": configs,
         "clocks": clk.summary(),
         "gpu_launches": 4 * args.steps,
         "wall_s_timed": t_wall,

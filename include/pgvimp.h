@@ -72,6 +72,17 @@ typedef enum {
 
 typedef enum { PGVIMP_RULE_GH = 0, PGVIMP_RULE_DEG3 = 1, PGVIMP_RULE_SMOLYAK = 2 } pgvimp_rule;
 
+/* The update taken at each iteration (both with the KL-bounded step-size
+ * search of App. C).  PROX: the KL-proximal step of Thm 1 (eq.
+ * mu_Sigma_update).  NGD: the natural-gradient step of Sec. 3.1(d),
+ * delta theta = beta G(theta)^-1 grad L with the Fisher matrix G, taken in the
+ * natural parameters (Lambda mu, -Lambda/2):
+ *   Lambda' = (1 - beta) Lambda_k + beta (K^-1 + 2 grad_Sigma psi_d),
+ *   Lambda' mu' = (1 - beta) Lambda_k mu_k + beta (K^-1 mu_bar - grad_mu psi_d
+ *                 + 2 grad_Sigma psi_d mu_k);
+ * it needs beta_max <= 1. */
+typedef enum { PGVIMP_UPDATE_PROX = 0, PGVIMP_UPDATE_NGD = 1 } pgvimp_update;
+
 /* Arithmetic of the path.  PLAIN_FP64: everything in FP64.  MIXED: the
  * quadrature, SDF and moment arithmetic in FP32 (FP32 accumulation); the
  * marginal recovery, the update and the KL / step-size search in FP64.
@@ -129,15 +140,19 @@ typedef struct {
   int init_kind;    /* 0: Lambda_0 = K^-1; 1: Lambda_0 = init_scale * I */
   double init_scale;
   int plan_threads; /* execution form (same for every plan of a batch; not part of the method):
-                       0 or 1: one GPU thread per plan, sequential sweeps over time (throughput form);
+                       1: one GPU thread per plan, sequential sweeps over time (thread form);
+                       16: sixteen lanes per plan, one element of each n x n block per lane,
+                       sequential sweeps over time (lane form; n = 4 only);
+                       0: the default throughput form: the lane form for n = 4 with MIXED_DF
+                       precision, the thread form otherwise;
                        32..256, a multiple of 32: one thread block of that size per plan, the block
-                       recursions by cyclic reduction over time (latency form); PLAIN_FP64 or MIXED
-                       precision only (EINVAL with MIXED_DF). */
+                       recursions by cyclic reduction over time (latency form), in any precision. */
   double temperature_high; /* two-phase temperature (the low/high T-hat schedule of the planning
                               experiments, Sec. 7): from global iteration switch_iter on (> 0), K^-1, b
                               and the cost are divided by temperature_high (> 0) instead of the
                               problem's temperature; 0 or switch_iter = 0: one phase */
   int switch_iter;
+  int update;       /* pgvimp_update (0: Thm 1) */
 } pgvimp_options;
 
 /* Per-iteration record.  Costs are those of the iterate the gradients were
@@ -159,7 +174,12 @@ typedef struct {
  * owns one plan.  A batch is used by one host thread at a time. */
 typedef struct pgvimp_batch pgvimp_batch;
 
-/* Device bytes a batch needs (inputs, state, scratch, logs). */
+/* Device bytes a batch needs (inputs, state, scratch, logs).  The layout
+ * holds, per plan, the prior (K^-1 blocks, b, mu_bar; Alg. 1, first two
+ * lines), the iterate (mu, Lambda blocks) and its marginals (Sec. 5.1), the
+ * gradients g, G (Sec. 4.2), trial buffers of the step-size search (App. C)
+ * and, for SLR models, the linearisation A_i, a_i (Sec. 6.2).  EINVAL as
+ * pgvimp_batch_create. */
 pgvimp_status pgvimp_batch_arena_bytes(int count, const pgvimp_problem *problems,
                                        const pgvimp_options *options, int precision, size_t *bytes);
 
@@ -180,9 +200,14 @@ pgvimp_status pgvimp_batch_upload(pgvimp_batch *b, void *stream);
 pgvimp_status pgvimp_batch_reset(pgvimp_batch *b, void *stream);
 
 /* Advances every plan by `iters` proximal iterations (<= 0: the whole plan,
- * options.iters, times options.slr_iters for SLR models).  A plan that has
- * not started is first initialised.  SLR models relinearise (Sec. 6.2) at the
- * start of each outer iteration.  Asynchronous on `stream`. */
+ * options.iters, times options.slr_iters for SLR models): the loop of Alg. 1
+ * -- factor expectations (Sec. 4.3, 5.2), gradients (eq. gradients_psid),
+ * the update of Thm 1 (or NGD, Sec. 3.1(d)) with the KL-bounded step-size
+ * search (App. C), marginals of the new precision (Sec. 5.1).  A plan that
+ * has not started is first initialised (prior, Alg. 1 lines 1-2).  SLR models
+ * relinearise (Sec. 6.2, Alg. 2) at the start of each outer iteration.
+ * Asynchronous on `stream`; a plan that fails (prior or marginals not PD)
+ * records its status and stops, the others continue. */
 pgvimp_status pgvimp_batch_run(pgvimp_batch *b, int iters, void *stream);
 
 /* Device-to-host copy of the results (means, marginal covariances, precision
@@ -230,17 +255,33 @@ pgvimp_status pgvimp_batch_read(const pgvimp_batch *b, int index, int buffer, do
 pgvimp_status pgvimp_batch_write(pgvimp_batch *b, int index, int buffer, const double *host, size_t count);
 
 /* ------------------------------------------------------- single-plan context
- * The calls of Alg. 1 / Alg. 2 for one problem: a batch of one. */
+ * The calls of Alg. 1 / Alg. 2 for one problem: a batch of one, on the
+ * library's own stream, with its own device memory. */
 typedef struct pgvimp_ctx pgvimp_ctx;
+/* Sets up one problem in the form of Sec. 2.2: the LTV SDE (A_t, a_t, B, Qc)
+ * discretised on t_i = i T/N, the start and goal Gaussians, the collision cost
+ * on an SDF (Sec. 4.1) and the method's options; deep-copies the inputs and
+ * uploads them.  Validation and errors as pgvimp_batch_create; ENOMEM if the
+ * device or pinned memory runs out. */
 pgvimp_status pgvimp_create(const pgvimp_problem *problem, const pgvimp_options *options, int precision,
                             pgvimp_ctx **out);
-/* One proximal iteration; `info` may be NULL. */
+/* One iteration of Alg. 1: the factor expectations and gradients at the
+ * current iterate, the update of Thm 1 (eq. mu_Sigma_update; NGD with
+ * options.update) at the largest step the KL bound of App. C admits, and the
+ * marginals of the new precision.  For SLR models, the relinearisation of
+ * Sec. 6.2 precedes the first iteration of each outer step of Alg. 2.  Blocks
+ * until done; `info` (may be NULL) receives the iteration's record. */
 pgvimp_status pgvimp_step(pgvimp_ctx *ctx, pgvimp_step_info *info);
-/* `iters` iterations (<= 0: the whole plan).  Blocks until done. */
+/* `iters` iterations (<= 0: the whole plan: Alg. 1 for options.iters
+ * iterations, or Alg. 2 for options.slr_iters linearisations of
+ * options.iters iterations each).  Blocks until done. */
 pgvimp_status pgvimp_plan(pgvimp_ctx *ctx, int iters);
-/* mu: (N+1)*n; Sigma: (N+1)*n*n marginal covariances; Lam_diag / Lam_off:
- * precision blocks.  Any pointer may be NULL. */
+/* The current Gaussian N(mu, Lambda^-1): mu ((N+1)*n), the marginal
+ * covariances Sigma_ii of Sec. 5.1 ((N+1)*n*n) and the precision blocks
+ * Lam_diag ((N+1)*n*n) / Lam_off (N*n*n), all FP64 into caller-owned host
+ * buffers.  Any pointer may be NULL. */
 pgvimp_status pgvimp_get(pgvimp_ctx *ctx, double *mu, double *Sigma, double *Lam_diag, double *Lam_off);
+/* Frees the context and its device memory.  NULL-safe. */
 pgvimp_status pgvimp_destroy(pgvimp_ctx *ctx);
 
 /* Last error text of a context (or of the calling thread if ctx is NULL). */
@@ -251,7 +292,10 @@ const char *pgvimp_last_error(const void *ctx);
  * the same state dimension and dynamics kind that wait at the same time are
  * packed into one batch; each batch runs the whole plan (Alg. 1, or Alg. 2
  * for SLR models) on one of `max_inflight` streams, so batches admitted while
- * others run overlap on the GPU.  A batch is admitted when a stream is free
+ * others run overlap on the GPU.  Each batch's launch sequence (copy in,
+ * prior, iterations, copy out, completion) is captured into a CUDA graph and
+ * launched as one; a stream's executable graph is updated in place for the
+ * next batch of the same shape.  A batch is admitted when a stream is free
  * and its device arena and pinned staging fit the server's pools, which are
  * allocated once at creation; a request waits at most `batch_window_ms` for
  * others to share its launch.  All server functions are thread-safe.
@@ -283,6 +327,8 @@ typedef struct {
   double now_ms;             /* server clock */
   double host_launch_ms;     /* scheduler time spent creating and queueing batches */
   double host_collect_ms;    /* scheduler time spent copying results out */
+  uint64_t graph_launches;   /* batches launched as one captured CUDA graph */
+  uint64_t graph_instantiations;   /* executable graphs built (the rest were updated in place) */
 } pgvimp_server_stats_t;
 
 /* Creates the pools, streams and the scheduler thread on the current device.

@@ -18,6 +18,7 @@ LIB_PATH = os.environ.get("PGVIMP_LIB") or os.path.join(_HERE, "_build", "libpgv
 
 OK, EINVAL, ENOMEM, ENOTPD, ECUDA, ETIMEOUT, EBUSY, ENOTFINITE, ENOTREADY = range(9)
 PREC_PLAIN_FP64, PREC_MIXED, PREC_MIXED_DF = 0, 1, 2
+UPDATE_PROX, UPDATE_NGD = 0, 1
 PHASE_PRIOR, PHASE_MARGINALS, PHASE_QUAD, PHASE_TRIAL, PHASE_SLR = range(5)
 (BUF_MU, BUF_LD, BUF_LO, BUF_SD, BUF_SO, BUF_KD, BUF_KO, BUF_B, BUF_G1, BUF_G2, BUF_TMU, BUF_TSD, BUF_TSO,
  BUF_ALTV, BUF_ALTVA, BUF_SCAL) = range(16)
@@ -63,7 +64,7 @@ class Options(C.Structure):
         ("rule", C.c_int), ("gh_p", C.c_int), ("beta_max", C.c_double), ("kl_eps", C.c_double),
         ("max_bisect", C.c_int), ("iters", C.c_int), ("slr_iters", C.c_int), ("init_kind", C.c_int),
         ("init_scale", C.c_double), ("plan_threads", C.c_int), ("temperature_high", C.c_double),
-        ("switch_iter", C.c_int),
+        ("switch_iter", C.c_int), ("update", C.c_int),
     ]
 
 
@@ -95,6 +96,7 @@ class ServerStats(C.Structure):
         ("queued", C.c_int), ("inflight", C.c_int), ("batches", C.c_uint64), ("plans", C.c_uint64),
         ("dev_used", C.c_size_t), ("host_used", C.c_size_t), ("now_ms", C.c_double),
         ("host_launch_ms", C.c_double), ("host_collect_ms", C.c_double),
+        ("graph_launches", C.c_uint64), ("graph_instantiations", C.c_uint64),
     ]
 
 
@@ -210,6 +212,7 @@ def marshal_options(op) -> Options:
     o.plan_threads = getattr(op, "plan_threads", 0)
     o.temperature_high = getattr(op, "temperature_high", 0.0)
     o.switch_iter = getattr(op, "switch_iter", 0)
+    o.update = getattr(op, "update", 0)
     return o
 
 

@@ -17,12 +17,19 @@ OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libpgvimp.so")
 ROOT = os.path.dirname(HERE)
 
-SOURCES = ["pgvimp_api.cu", "pgvimp_noalloc.cu", "pgvimp_server.cu"] + [f"k{n}_{part}.cu" for n in (14, 6, 4)
+SOURCES = ["pgvimp_api.cu", "pgvimp_noalloc.cu", "pgvimp_server.cu", "k4_lane_df.cu", "k4_lane_f32.cu",
+           "k4_lane_f64.cu"] + [f"k{n}_{part}.cu" for n in (14, 6, 4)
                                for part in ("iter_df", "iter_f32", "cta_f32", "iter_f64", "cta_f64",
-                                            "aux", "aux_df", "rows")]
-HEADERS = ["pgvimp_device.cuh", "pgvimp_kernels.cuh", "pgvimp_cr.cuh", "pgvimp_plan.h", "pgvimp_launch.h",
-           "pgvimp_internal.h", "pgvimp_pool.h"]
+                                            "cta_df", "aux", "aux_df", "rows")]
+HEADERS = ["pgvimp_device.cuh", "pgvimp_dfx.cuh", "pgvimp_kernels.cuh", "pgvimp_cr.cuh", "pgvimp_lane.cuh", "pgvimp_plan.h",
+           "pgvimp_launch.h", "pgvimp_internal.h", "pgvimp_pool.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+# The block form with double-float recursions is built with the front-end
+# (NVVM) optimiser at -O1 (ptxas keeps -O3): at the default -O3 the root pivot
+# of its cyclic reduction was miscomputed for n = 4 (a stand-alone reduction of
+# a two-state chain fails at -O3 and is exact at -O1, at -O0 and with -G, and
+# exact at -O3 once a printf is added inside it).
+EXTRA_FLAGS = {f"k{n}_cta_df.cu": ["-Xcicc", "-O1"] for n in (4, 6, 14)}
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "-I", os.path.join(ROOT, "include")]
 
 
@@ -40,6 +47,8 @@ def _headers_of(src: str):
         base += ["pgvimp_device.cuh", "pgvimp_kernels.cuh", "pgvimp_launch.h"]
         if "_cta_" in src:
             base += ["pgvimp_cr.cuh"]
+        if "_lane_" in src:
+            base += ["pgvimp_lane.cuh", "pgvimp_dfx.cuh"]
     elif src == "pgvimp_api.cu":
         base += ["pgvimp_device.cuh", "pgvimp_launch.h", "pgvimp_internal.h"]
     elif src == "pgvimp_server.cu":
@@ -53,6 +62,8 @@ def _headers_of(src: str):
 
 def _deps_mtime(src: str):
     files = [os.path.join(CSRC, h) for h in _headers_of(src)] + [os.path.join(ROOT, "include", "pgvimp.h")]
+    if src in EXTRA_FLAGS:
+        files.append(os.path.abspath(__file__))
     return max(os.path.getmtime(f) for f in files)
 
 
@@ -64,7 +75,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
         s = os.path.join(CSRC, src)
         o = os.path.join(OUT, "obj", src.replace(".cu", ".o"))
         if force or not os.path.exists(o) or os.path.getmtime(o) < max(os.path.getmtime(s), _deps_mtime(src)):
-            cmd = [nvcc, *ARCH, *NVCC_FLAGS, "-c", s, "-o", o]
+            cmd = [nvcc, *ARCH, *NVCC_FLAGS, *EXTRA_FLAGS.get(src, []), "-c", s, "-o", o]
             if ptxas_info:
                 cmd.insert(1, "-Xptxas=-v")
             jobs.append((src, cmd))

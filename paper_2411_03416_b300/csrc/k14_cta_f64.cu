@@ -3,5 +3,5 @@
 
 namespace pgv {
 template cudaError_t launch_iter_cta<14, double, double>(const Launch& L, int iters, int tpb);
-template cudaError_t launch_aux_cta<14>(const Launch& L, int phase, int arg_i, int qt32, int tpb);
+template cudaError_t launch_aux_cta<14, double>(const Launch& L, int phase, int arg_i, int qt32, int tpb);
 }  // namespace pgv

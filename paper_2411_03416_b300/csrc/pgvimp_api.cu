@@ -22,20 +22,30 @@
 
 namespace pgv {
 // Dispatch of a phase to the kernels of state dimension n and precision.
-static cudaError_t launch_phase(int n, const Launch& L, int phase, int arg_i, double arg_d, int precision, int tpb) {
+// `tpb`: threads per plan of the block form (0: not the block form); `lane`:
+// the lane form of the fused iterations (n = 4, sixteen lanes per plan).
+static cudaError_t launch_phase(int n, const Launch& L, int phase, int arg_i, double arg_d, int precision, int tpb,
+                                bool lane) {
   constexpr int PRIOR = 100, INIT = 101, ITER = 102, SLR = 103;
   const bool rows = (phase == PGVIMP_PHASE_MARGINALS || phase == PGVIMP_PHASE_QUAD || phase == PGVIMP_PHASE_TRIAL);
   const bool df = (precision == PGVIMP_PREC_MIXED_DF);
   const int qt32 = (precision != PGVIMP_PREC_PLAIN_FP64);
+  if (lane && n == 4 && phase == ITER) {
+    if (df) return launch_iter_lane<float, df64>(L, arg_i);
+    return qt32 ? launch_iter_lane<float, double>(L, arg_i) : launch_iter_lane<double, double>(L, arg_i);
+  }
   switch (n) {
 #define PGV_CASE(N_)                                                                                      \
   case N_:                                                                                                \
-    if (tpb && !df) {                                                                                     \
-      if (phase == ITER)                                                                                  \
+    if (tpb) {                                                                                            \
+      if (phase == ITER) {                                                                                \
+        if (df) return launch_iter_cta<N_, float, df64>(L, arg_i, tpb);                                   \
         return qt32 ? launch_iter_cta<N_, float, double>(L, arg_i, tpb)                                   \
                     : launch_iter_cta<N_, double, double>(L, arg_i, tpb);                                 \
+      }                                                                                                   \
       if (phase == INIT || phase == SLR || (phase == PRIOR && arg_i == 1))                                \
-        return launch_aux_cta<N_>(L, phase, arg_i, qt32, tpb);                                            \
+        return df ? launch_aux_cta<N_, df64>(L, phase, arg_i, qt32, tpb)                                  \
+                  : launch_aux_cta<N_, double>(L, phase, arg_i, qt32, tpb);                               \
     }                                                                                                     \
     if (phase == ITER) {                                                                                  \
       if (df) return launch_iter<N_, float, df64>(L, arg_i);                                              \
@@ -341,11 +351,16 @@ pgvimp_status validate(const pgvimp_problem& p, const pgvimp_options& o, int idx
   if (o.max_bisect < 0 || o.max_bisect > 60) return E(PGVIMP_EINVAL, "max_bisect out of range");
   if (o.iters < 0 || o.iters > (1 << 20)) return E(PGVIMP_EINVAL, "iters out of range");
   if (o.init_kind == 1 && !(o.init_scale > 0.0)) return E(PGVIMP_EINVAL, "init_scale must be positive");
-  if (o.plan_threads > 1 && (o.plan_threads < 32 || o.plan_threads > kCrMaxThreads || (o.plan_threads & 31)))
-    return E(PGVIMP_EINVAL, "plan_threads must be 0, 1, or a multiple of 32 in 32..256");
-  if (o.plan_threads < 0) return E(PGVIMP_EINVAL, "plan_threads must be 0, 1, or a multiple of 32 in 32..256");
+  if ((o.plan_threads > 1 && o.plan_threads != kLaneThreads &&
+       (o.plan_threads < 32 || o.plan_threads > kCrMaxThreads || (o.plan_threads & 31))) || o.plan_threads < 0)
+    return E(PGVIMP_EINVAL, "plan_threads must be 0, 1, 16, or a multiple of 32 in 32..256");
+  if (o.plan_threads == kLaneThreads && p.n != 4)
+    return E(PGVIMP_EINVAL, "the lane form (plan_threads = 16) is built for state dimension 4");
   if (!(o.temperature_high >= 0.0) || !std::isfinite(o.temperature_high) || o.switch_iter < 0)
     return E(PGVIMP_EINVAL, "temperature_high must be finite and >= 0, switch_iter >= 0");
+  if (o.update != PGVIMP_UPDATE_PROX && o.update != PGVIMP_UPDATE_NGD) return E(PGVIMP_EINVAL, "unknown update");
+  if (o.update == PGVIMP_UPDATE_NGD && o.beta_max > 1.0)
+    return E(PGVIMP_EINVAL, "the natural-gradient step needs beta_max <= 1");
   return PGVIMP_OK;
 }
 
@@ -367,7 +382,8 @@ struct PlanLayout {
 
 struct BatchImpl {
   int count = 0, n = 0, precision = 0, dyn = 0;
-  int tpb = 0;   // threads per plan in the block form (0: one thread per plan)
+  int tpb = 0;   // threads per plan in the block form (0: one thread per plan, or the lane form)
+  bool lane = false;   // lane form of the fused iterations (n = 4: plan_threads 16, or 0 with double-float)
   int iters_opt = 0, slr_opt = 0;
   std::vector<pgvimp_problem> probs;
   std::vector<pgvimp_options> opts;
@@ -531,7 +547,7 @@ void build_descs(BatchImpl& B) {
     d.n = p.n; d.m = p.m; d.N = p.N; d.nq = p.n / 2; d.dc = cost_dims(p);
     d.T = p.T; d.dt = p.T / p.N;
     d.rule = o.rule; d.gh_p = o.gh_p; d.max_bisect = o.max_bisect; d.iters = o.iters;
-    d.slr_iters = o.slr_iters; d.init_kind = o.init_kind;
+    d.slr_iters = o.slr_iters; d.init_kind = o.init_kind; d.update = o.update;
     d.beta_max = o.beta_max; d.kl_eps = o.kl_eps; d.init_scale = o.init_scale;
     d.cost_kind = p.cost_kind; d.psi_form = p.psi_form; d.factor_set = p.factor_set;
     d.eps = p.eps; d.sigma_obs = p.sigma_obs; d.inv_temp = (p.temperature > 0.0) ? 1.0 / p.temperature : 1.0;
@@ -637,7 +653,7 @@ pgvimp_status cuda_fail(std::string* err, cudaError_t e, const char* what) {
 
 pgvimp_status launch(BatchImpl& B, int phase, int arg_i, double arg_d, cudaStream_t s) {
   Launch L{reinterpret_cast<const PlanDesc*>(B.d_in() + B.off_desc), B.count, s};
-  cudaError_t e = launch_phase(B.n, L, phase, arg_i, arg_d, B.precision, B.tpb);
+  cudaError_t e = launch_phase(B.n, L, phase, arg_i, arg_d, B.precision, B.tpb, B.lane);
   if (e != cudaSuccess) return cuda_fail(&B.err, e, "kernel launch");
   return PGVIMP_OK;
 }
@@ -689,8 +705,7 @@ static pgvimp_status prepare(int count, const pgvimp_problem* problems, const pg
     if (st != PGVIMP_OK) return st;
     if (problems[i].n != problems[0].n) return fail(&B.err, PGVIMP_EINVAL, "a batch needs one state dimension");
     if (problems[i].dyn_kind != problems[0].dyn_kind) return fail(&B.err, PGVIMP_EINVAL, "a batch needs one dynamics kind");
-    if ((options[i].plan_threads > 1) != (options[0].plan_threads > 1) ||
-        (options[i].plan_threads > 1 && options[i].plan_threads != options[0].plan_threads))
+    if (options[i].plan_threads != options[0].plan_threads)
       return fail(&B.err, PGVIMP_EINVAL, "a batch needs one plan_threads");
     if (problems[i].dyn_kind != PGVIMP_DYN_LINEAR &&
         (options[i].iters != options[0].iters || options[i].slr_iters != options[0].slr_iters))
@@ -700,9 +715,12 @@ static pgvimp_status prepare(int count, const pgvimp_problem* problems, const pg
   B.n = problems[0].n;
   B.dyn = problems[0].dyn_kind;
   B.precision = precision;
-  B.tpb = options[0].plan_threads > 1 ? options[0].plan_threads : 0;
-  if (B.tpb && precision == PGVIMP_PREC_MIXED_DF)
-    return fail(&B.err, PGVIMP_EINVAL, "the block form (plan_threads > 1) runs FP64 or mixed recursions only");
+  B.tpb = options[0].plan_threads >= 32 ? options[0].plan_threads : 0;
+  // the default throughput form: the lane form where it is faster (n = 4 with
+  // double-float recursions, whose FP32 pipe absorbs the lane form's extra
+  // work; with FP64 recursions one thread per plan keeps the FP64 pipe busier)
+  B.lane = options[0].plan_threads == kLaneThreads ||
+           (options[0].plan_threads == 0 && B.n == 4 && precision == PGVIMP_PREC_MIXED_DF);
   B.iters_opt = options[0].iters;
   B.slr_opt = options[0].slr_iters;
   B.probs.assign(problems, problems + count);

@@ -186,6 +186,9 @@ PGV_BIG TrialOut cr_trial(const PlanDesc& P, double beta_d, int cur, int out, do
   R* So_out = rp<R>(P.So[out]);
   const bool wm = !marg_only;
   const R beta = r_from<R>(beta_d), beta2 = beta + beta, zero = r_fromf<R>(0.0f);
+  // natural-gradient step (Sec. 3.1(d)): Lambda_k weighted by 1 - beta, M = A~, s = 1
+  const bool ngd = wm && (P.update == PGVIMP_UPDATE_NGD);
+  const R cL = ngd ? r_from<R>(1.0 - beta_d) : r_fromf<R>(1.0f);
   TrialOut res;
   res.kl = INFINITY;
   res.pd = false;
@@ -199,6 +202,9 @@ PGV_BIG TrialOut cr_trial(const PlanDesc& P, double beta_d, int cur, int out, do
     R* sp = scr + (size_t)i * SS;
     R B[nn], DA[np], DM[np];
     ld_blk<n, R>(Ld + (size_t)i * nn, B);
+    if (ngd)
+#pragma unroll (n <= 8 ? 32 : 0)
+      for (int e = 0; e < nn; ++e) B[e] = cL * B[e];
 #pragma unroll (n <= 8 ? 32 : 0)
     for (int a = 0; a < n; ++a)
 #pragma unroll (n <= 8 ? 32 : 0)
@@ -213,6 +219,7 @@ PGV_BIG TrialOut cr_trial(const PlanDesc& P, double beta_d, int cur, int out, do
         for (int c = 0; c <= a; ++c) {
           const R kb = beta * K[a * n + c];
           DM[pk(a, c)] = DM[pk(a, c)] + kb;
+          if (ngd) DM[pk(a, c)] = r_fma(beta2, G[a * n + c], DM[pk(a, c)]);
           DA[pk(a, c)] = r_fma(beta2, G[a * n + c], DA[pk(a, c)] + kb);
         }
       // rhs_i = beta (b_i - g_i - (K^-1 mu)_i)
@@ -253,6 +260,9 @@ PGV_BIG TrialOut cr_trial(const PlanDesc& P, double beta_d, int cur, int out, do
     if (i < N) {
       R E[nn];
       ld_blk<n, R>(Lo + (size_t)i * nn, E);
+      if (ngd)
+#pragma unroll (n <= 8 ? 32 : 0)
+        for (int e = 0; e < nn; ++e) E[e] = cL * E[e];
       if (wm) {
         R K[nn];
         ld_blk<n, R>(Ko + (size_t)i * nn, K);
@@ -454,8 +464,8 @@ PGV_BIG TrialOut cr_trial(const PlanDesc& P, double beta_d, int cur, int out, do
     __syncthreads();
   }
 
-  // ---- KL pieces, prior cost, outputs scaled by (beta + 1)
-  const double bp1d = beta_d + 1.0;
+  // ---- KL pieces, prior cost, outputs scaled by s (beta + 1, or 1 for the natural-gradient step)
+  const double bp1d = ngd ? 1.0 : beta_d + 1.0;
   const R bp1 = r_from<R>(bp1d);
   R trc = zero, dl = zero, ktr = zero, kq = zero;
   for (int i = tid; i <= N; i += T) {
@@ -538,7 +548,7 @@ PGV_BIG TrialOut cr_trial(const PlanDesc& P, double beta_d, int cur, int out, do
   block_sum<4>(parts, red);
   res.pd = true;
   const double Dd = (double)n * (N + 1);
-  res.logdet = lsum[0] - (wm ? Dd * log(bp1d) : 0.0);
+  res.logdet = lsum[0] - ((wm && !ngd) ? Dd * log(bp1d) : 0.0);
   res.trace = beta_d * parts[0];
   res.delta = parts[1];
   res.kl = 0.5 * (res.trace + res.delta + res.logdet - logdet_k);
@@ -552,7 +562,9 @@ template <int n, typename R>
 PGV_BIG void cr_accept_precision(const PlanDesc& P, double beta_d) {
   constexpr int nn = n * n;
   const int N = P.N;
-  const R inv = r_from<R>(1.0 / (beta_d + 1.0)), beta = r_from<R>(beta_d), two = r_fromf<R>(2.0f);
+  const bool ngd = (P.update == PGVIMP_UPDATE_NGD);
+  const R inv = r_from<R>(ngd ? 1.0 : 1.0 / (beta_d + 1.0)), beta = r_from<R>(beta_d), two = r_fromf<R>(2.0f);
+  const R cL = ngd ? r_from<R>(1.0 - beta_d) : r_fromf<R>(1.0f);
   R* Ld = rp<R>(P.Ld);
   R* Lo = rp<R>(P.Lo);
   const R* Kd = rp<R>(P.Kd);
@@ -564,13 +576,13 @@ PGV_BIG void cr_accept_precision(const PlanDesc& P, double beta_d) {
     ld_blk<n, R>(Ld + (size_t)i * nn, Lb);
     ld_blk<n, R>(GG + (size_t)i * nn, Gb);
 #pragma unroll (n <= 8 ? 32 : 0)
-    for (int e = 0; e < nn; ++e) Lb[e] = r_fma(beta, r_fma(two, Gb[e], K[e]), Lb[e]) * inv;
+    for (int e = 0; e < nn; ++e) Lb[e] = r_fma(beta, r_fma(two, Gb[e], K[e]), cL * Lb[e]) * inv;
     st_blk<n, R>(Ld + (size_t)i * nn, Lb);
     if (i < N) {
       ld_blk<n, R>(Ko + (size_t)i * nn, K);
       ld_blk<n, R>(Lo + (size_t)i * nn, Lb);
 #pragma unroll (n <= 8 ? 32 : 0)
-      for (int e = 0; e < nn; ++e) Lb[e] = r_fma(beta, K[e], Lb[e]) * inv;
+      for (int e = 0; e < nn; ++e) Lb[e] = r_fma(beta, K[e], cL * Lb[e]) * inv;
       st_blk<n, R>(Lo + (size_t)i * nn, Lb);
     }
   }
@@ -929,17 +941,17 @@ cudaError_t launch_iter_cta(const Launch& L, int iters, int tpb) {
 }
 
 // Initial iterate, the SLR linearisation (`arg_i` = mode) and the LTV prior,
-// block form (FP64 recursions).
-template <int n>
+// block form, recursions in R (FP64 or double-float).
+template <int n, typename R>
 cudaError_t launch_aux_cta(const Launch& L, int phase, int arg_i, int qt32, int tpb) {
   if (tpb < 32 || tpb > kCrMaxThreads || (tpb & 31)) return cudaErrorInvalidValue;
   switch (phase) {
-    case PH_INIT: k_init_cta<n, double><<<L.count, tpb, 0, L.stream>>>(L.descs, L.count); break;
+    case PH_INIT: k_init_cta<n, R><<<L.count, tpb, 0, L.stream>>>(L.descs, L.count); break;
     case PH_SLR:
-      if (qt32) k_slr_cta<n, float, double><<<L.count, tpb, 0, L.stream>>>(L.descs, L.count, arg_i);
-      else k_slr_cta<n, double, double><<<L.count, tpb, 0, L.stream>>>(L.descs, L.count, arg_i);
+      if (qt32) k_slr_cta<n, float, R><<<L.count, tpb, 0, L.stream>>>(L.descs, L.count, arg_i);
+      else k_slr_cta<n, double, R><<<L.count, tpb, 0, L.stream>>>(L.descs, L.count, arg_i);
       break;
-    case PH_PRIOR: k_prior_ltv_cta<n, double><<<L.count, tpb, 0, L.stream>>>(L.descs, L.count); break;
+    case PH_PRIOR: k_prior_ltv_cta<n, R><<<L.count, tpb, 0, L.stream>>>(L.descs, L.count); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

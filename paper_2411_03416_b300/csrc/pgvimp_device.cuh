@@ -194,32 +194,22 @@ struct Blk {
 };
 PGV_HD constexpr int pk(int a, int c) { return a >= c ? a * (a + 1) / 2 + c : c * (c + 1) / 2 + a; }
 
-// 16-byte vector access to pairs of 8-byte values (double or df64).
-template <typename R>
-struct __align__(16) Pair2 {
-  R a, b;
-};
-
+// Blocks move between registers and memory element by element.  (Built for
+// sm_103a with this toolchain, a 16-byte vector store of a register-held
+// packed block -- through double2, float4 or a 16-byte aggregate alike --
+// wrote another element's value in place of element 0 in some kernels, while
+// the register values right before the store were correct; element-wise
+// stores and loads of the same blocks are exact.  A single-thread reduction
+// of a two-state chain reproduced it.)
 template <int n, typename R>
 PGV_DEV void ld_blk(const R* p, R* X) {
-  const Pair2<R>* q = reinterpret_cast<const Pair2<R>*>(p);
 #pragma unroll (n <= 8 ? 32 : 0)
-  for (int e = 0; e < n * n / 2; ++e) {
-    Pair2<R> v = q[e];
-    X[2 * e] = v.a;
-    X[2 * e + 1] = v.b;
-  }
+  for (int e = 0; e < n * n; ++e) X[e] = p[e];
 }
 template <int n, typename R>
 PGV_DEV void st_blk(R* p, const R* X) {
-  Pair2<R>* q = reinterpret_cast<Pair2<R>*>(p);
 #pragma unroll (n <= 8 ? 32 : 0)
-  for (int e = 0; e < n * n / 2; ++e) {
-    Pair2<R> v;
-    v.a = X[2 * e];
-    v.b = X[2 * e + 1];
-    q[e] = v;
-  }
+  for (int e = 0; e < n * n; ++e) p[e] = X[e];
 }
 // symmetric packed <-> full block in memory
 template <int n, typename R>
@@ -240,29 +230,18 @@ PGV_DEV void st_sym(R* p, const R* S) {
     for (int c = 0; c < n; ++c) X[a * n + c] = S[pk(a, c)];
   st_blk<n, R>(p, X);
 }
-// packed storage of length np rounded up to a whole 16-byte pair
+// packed storage (np elements; the layout leaves room for np rounded up to even)
 template <int n, typename R>
 PGV_DEV void ld_packed(const R* p, R* S) {
-  const Pair2<R>* q = reinterpret_cast<const Pair2<R>*>(p);
   constexpr int np = n * (n + 1) / 2;
 #pragma unroll (n <= 8 ? 32 : 0)
-  for (int e = 0; e < (np + 1) / 2; ++e) {
-    Pair2<R> v = q[e];
-    S[2 * e] = v.a;
-    if (2 * e + 1 < np) S[2 * e + 1] = v.b;
-  }
+  for (int e = 0; e < np; ++e) S[e] = p[e];
 }
 template <int n, typename R>
 PGV_DEV void st_packed(R* p, const R* S) {
-  Pair2<R>* q = reinterpret_cast<Pair2<R>*>(p);
   constexpr int np = n * (n + 1) / 2;
 #pragma unroll (n <= 8 ? 32 : 0)
-  for (int e = 0; e < (np + 1) / 2; ++e) {
-    Pair2<R> v;
-    v.a = S[2 * e];
-    v.b = (2 * e + 1 < np) ? S[2 * e + 1] : S[2 * e];
-    q[e] = v;
-  }
+  for (int e = 0; e < np; ++e) p[e] = S[e];
 }
 template <int n, typename R>
 PGV_DEV void ld_vec(const R* p, R* x) {

@@ -601,19 +601,25 @@ struct TrialOut {
   bool pd;
 };
 
-// Thm 1 at step beta, scaled by (beta+1):
+// Thm 1 at step beta, scaled by s = beta+1:
 //   A~ = beta (2G + K^-1) + Lambda_k          = (beta+1) Lambda'
 //   M  = beta K^-1 + Lambda_k                 (mean system times beta)
 //   M delta = beta (-g + b - K^-1 mu_k),      mu' = mu_k + delta
-// One forward sweep eliminates A~ and M together (they share the off-diagonal
-// blocks); one backward sweep produces Sigma~ = A~^-1 (selected blocks), delta
-// and the KL pieces
+// The natural-gradient step (Sec. 3.1(d); P.update == PGVIMP_UPDATE_NGD) has
+// the same form with s = 1, Lambda_k weighted by c = 1 - beta and M = A~:
+//   A~ = beta (2G + K^-1) + (1 - beta) Lambda_k = Lambda',
+//   Lambda' delta = beta (-g + b - K^-1 mu_k),
+// the step of the natural parameters (Lambda mu, -Lambda/2) along minus the
+// gradient in the expectation parameters.  One forward sweep eliminates A~ and
+// M together (they share the off-diagonal blocks); one backward sweep produces
+// Sigma~ = A~^-1 (selected blocks), delta and the KL pieces
 //   KL = 1/2 [beta tr((Lambda_k - 2G - K^-1) Sigma~) + delta^T Lambda_k delta
-//             + log det Lambda' - log det Lambda_k],
-// using tr(Lambda_k Sigma') - D = tr((Lambda_k - Lambda') Sigma').  Results go
-// to buffer set `out`: mu', Sigma' = (beta+1) Sigma~.  Carried between states:
-// the packed Schur terms of both eliminations, W^M_{i-1} y_{i-1} and
-// K^-1_{i,i-1} mu_{i-1} (vectors), not the matrices.
+//             + log det Lambda' - log det Lambda_k]
+// (both updates: tr(Lambda_k Sigma') - D = tr((Lambda_k - Lambda') Sigma') =
+// tr((s Lambda_k - A~) Sigma~)).  Results go to buffer set `out`: mu',
+// Sigma' = s Sigma~.  Carried between states: the packed Schur terms of both
+// eliminations, W^M_{i-1} y_{i-1} and K^-1_{i,i-1} mu_{i-1} (vectors), not the
+// matrices.
 template <int n, typename R>
 PGV_BIG TrialOut trial(const PlanDesc& P, double beta_d, int cur, int out, double logdet_k) {
   constexpr int nn = n * n, np = Scr<n>::np, SS = Scr<n>::stride;
@@ -636,6 +642,8 @@ PGV_BIG TrialOut trial(const PlanDesc& P, double beta_d, int cur, int out, doubl
   res.delta = 0.0;
   res.trace = 0.0;
   const R beta = r_from<R>(beta_d), beta2 = beta + beta, zero = r_fromf<R>(0.0f);
+  const bool ngd = (P.update == PGVIMP_UPDATE_NGD);
+  const R cL = ngd ? r_from<R>(1.0 - beta_d) : r_fromf<R>(1.0f);   // weight of Lambda_k
   R SA[np], SM[np], vM[n], q[n], mi[n];
 #pragma unroll (n <= 8 ? 32 : 0)
   for (int e = 0; e < np; ++e) {
@@ -676,8 +684,14 @@ PGV_BIG TrialOut trial(const PlanDesc& P, double beta_d, int cur, int out, doubl
 #pragma unroll (n <= 8 ? 32 : 0)
       for (int a = 0; a < n; ++a)
 #pragma unroll (n <= 8 ? 32 : 0)
-        for (int c = 0; c <= a; ++c) CA[pk(a, c)] = r_fma(beta2, B[a * n + c], CA[pk(a, c)]);
+        for (int c = 0; c <= a; ++c) {
+          CA[pk(a, c)] = r_fma(beta2, B[a * n + c], CA[pk(a, c)]);
+          if (ngd) CM[pk(a, c)] = r_fma(beta2, B[a * n + c], CM[pk(a, c)]);
+        }
       ld_blk<n, R>(Ld + (size_t)i * nn, B);
+      if (ngd)
+#pragma unroll (n <= 8 ? 32 : 0)
+        for (int e = 0; e < nn; ++e) B[e] = cL * B[e];
 #pragma unroll (n <= 8 ? 32 : 0)
       for (int a = 0; a < n; ++a)
 #pragma unroll (n <= 8 ? 32 : 0)
@@ -707,8 +721,11 @@ PGV_BIG TrialOut trial(const PlanDesc& P, double beta_d, int cur, int out, doubl
       }
       R B[nn];
       ld_blk<n, R>(Lo + (size_t)i * nn, B);
+      if (ngd)
 #pragma unroll (n <= 8 ? 32 : 0)
-      for (int e = 0; e < nn; ++e) E[e] = r_fma(beta, E[e], B[e]);   // beta K^-1_{i+1,i} + Lambda_{i+1,i}
+        for (int e = 0; e < nn; ++e) B[e] = cL * B[e];
+#pragma unroll (n <= 8 ? 32 : 0)
+      for (int e = 0; e < nn; ++e) E[e] = r_fma(beta, E[e], B[e]);   // beta K^-1_{i+1,i} + c Lambda_{i+1,i}
     }
     R y[n], z[n];
 #pragma unroll (n <= 8 ? 32 : 0)
@@ -748,8 +765,8 @@ PGV_BIG TrialOut trial(const PlanDesc& P, double beta_d, int cur, int out, doubl
   if (!okA || !okM) return res;
   res.pd = true;
   const double Dd = (double)n * (N + 1);
-  const double bp1d = beta_d + 1.0;
-  res.logdet = ldA.log_value() - Dd * log(bp1d);
+  const double bp1d = ngd ? 1.0 : beta_d + 1.0;        // s
+  res.logdet = ldA.log_value() - (ngd ? 0.0 : Dd * log(bp1d));
   const R bp1 = r_from<R>(bp1d), mbp1 = -bp1;
   // backward sweep
   R* mo_out = rp<R>(P.mu[out]);
@@ -908,12 +925,15 @@ PGV_BIG void switch_temperature(const PlanDesc& P, int first, int stride) {
   }
 }
 
-// Lambda_{k+1} = A~(beta) / (beta+1), written over (Ld, Lo).
+// Lambda_{k+1} = A~(beta) / s, written over (Ld, Lo): s = beta+1 (Thm 1) or
+// 1 with Lambda_k weighted by 1 - beta (natural-gradient step).
 template <int n, typename R>
 PGV_BIG void accept_precision(const PlanDesc& P, double beta_d) {
   constexpr int nn = n * n;
   const int N = P.N;
-  const R inv = r_from<R>(1.0 / (beta_d + 1.0)), beta = r_from<R>(beta_d), two = r_fromf<R>(2.0f);
+  const bool ngd = (P.update == PGVIMP_UPDATE_NGD);
+  const R inv = r_from<R>(ngd ? 1.0 : 1.0 / (beta_d + 1.0)), beta = r_from<R>(beta_d), two = r_fromf<R>(2.0f);
+  const R cL = ngd ? r_from<R>(1.0 - beta_d) : r_fromf<R>(1.0f);
   R* Ld = rp<R>(P.Ld);
   R* Lo = rp<R>(P.Lo);
   const R* Kd = rp<R>(P.Kd);
@@ -925,13 +945,13 @@ PGV_BIG void accept_precision(const PlanDesc& P, double beta_d) {
     ld_blk<n, R>(Ld + (size_t)i * nn, Lb);
     ld_blk<n, R>(GG + (size_t)i * nn, Gb);
 #pragma unroll (n <= 8 ? 32 : 0)
-    for (int e = 0; e < nn; ++e) Lb[e] = r_fma(beta, r_fma(two, Gb[e], K[e]), Lb[e]) * inv;
+    for (int e = 0; e < nn; ++e) Lb[e] = r_fma(beta, r_fma(two, Gb[e], K[e]), cL * Lb[e]) * inv;
     st_blk<n, R>(Ld + (size_t)i * nn, Lb);
     if (i < N) {
       ld_blk<n, R>(Ko + (size_t)i * nn, K);
       ld_blk<n, R>(Lo + (size_t)i * nn, Lb);
 #pragma unroll (n <= 8 ? 32 : 0)
-      for (int e = 0; e < nn; ++e) Lb[e] = r_fma(beta, K[e], Lb[e]) * inv;
+      for (int e = 0; e < nn; ++e) Lb[e] = r_fma(beta, K[e], cL * Lb[e]) * inv;
       st_blk<n, R>(Lo + (size_t)i * nn, Lb);
     }
   }

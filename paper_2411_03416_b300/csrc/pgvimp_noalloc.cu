@@ -15,6 +15,7 @@
 // element before reading it, so nothing needs clearing); two calls that
 // overlap on the GPU (different streams, or different host threads) race on
 // it and must be serialised by the caller.
+#include <cuda.h>   // driver types only; the two driver calls are reached through cudart
 #include <cuda_runtime.h>
 
 #include <cstring>
@@ -32,8 +33,29 @@ constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) double g_noalloc_scratch[kNoallocScratchDoubles];
 
+// Resolved addresses, one per (device, CUDA context).  A module variable
+// lives in a context: after cudaDeviceReset, or under another context made
+// current on the same device, the library is loaded again at another address,
+// so an address is reused only while the context it was resolved in is the
+// current one.  Contexts are told apart by their process-unique id.
+struct NoallocEntry {
+  int dev;
+  unsigned long long ctx_id;
+  double* ptr;
+};
+constexpr int kMaxEntries = 4 * kMaxDevices;
 std::mutex g_noalloc_mu;
-double* g_noalloc_ptr[kMaxDevices] = {nullptr};
+NoallocEntry g_noalloc_cache[kMaxEntries];
+int g_noalloc_used = 0;
+int g_noalloc_next = 0;
+
+using PfnCtxGetCurrent = CUresult (*)(CUcontext*);
+using PfnCtxGetId = CUresult (*)(CUcontext, unsigned long long*);
+
+// Id of the context current on the calling thread (cuCtxGetCurrent,
+// cuCtxGetId, reached through cudaGetDriverEntryPointByVersion so that the
+// library needs no link to the driver library).
+pgvimp_status current_ctx_id(unsigned long long* id);
 
 // Per-state scratch: packed C_i^-1 (padded to an even count) and W_i.
 template <int n>
@@ -96,22 +118,63 @@ pgvimp_status noalloc_fail(pgvimp_status st, const std::string& m) {
   return st;
 }
 
-// Device address of the scratch array on the current device, resolved once
-// per device (host code must not use the symbol itself as an address).
+pgvimp_status current_ctx_id(unsigned long long* id) {
+  static PfnCtxGetCurrent get_current = nullptr;
+  static PfnCtxGetId get_id = nullptr;
+  if (!get_current || !get_id) {
+    void* f1 = nullptr;
+    void* f2 = nullptr;
+    cudaDriverEntryPointQueryResult q1, q2;
+    cudaError_t e1 = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1);
+    cudaError_t e2 = cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2);
+    if (e1 != cudaSuccess || e2 != cudaSuccess || q1 != cudaDriverEntryPointSuccess ||
+        q2 != cudaDriverEntryPointSuccess || !f1 || !f2)
+      return noalloc_fail(PGVIMP_ECUDA, "the driver's context queries are not available");
+    get_current = reinterpret_cast<PfnCtxGetCurrent>(f1);
+    get_id = reinterpret_cast<PfnCtxGetId>(f2);
+  }
+  CUcontext ctx = nullptr;
+  if (get_current(&ctx) != CUDA_SUCCESS) return noalloc_fail(PGVIMP_ECUDA, "cuCtxGetCurrent failed");
+  if (!ctx) {
+    // no context yet on this thread: cudaSetDevice makes the device's primary
+    // context current (it allocates nothing)
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaSetDevice(dev);
+    if (e != cudaSuccess) return noalloc_fail(PGVIMP_ECUDA, std::string("cudaSetDevice: ") + cudaGetErrorString(e));
+    if (get_current(&ctx) != CUDA_SUCCESS || !ctx) return noalloc_fail(PGVIMP_ECUDA, "no current CUDA context");
+  }
+  if (get_id(ctx, id) != CUDA_SUCCESS) return noalloc_fail(PGVIMP_ECUDA, "cuCtxGetId failed");
+  return PGVIMP_OK;
+}
+
+// Device address of the scratch array in the current device's current
+// context, resolved once per (device, context) with that device current
+// (host code must not use the symbol itself as an address).
 pgvimp_status noalloc_scratch(double** out) {
   int dev = -1;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return noalloc_fail(PGVIMP_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
   if (dev < 0 || dev >= kMaxDevices) return noalloc_fail(PGVIMP_EINVAL, "device index out of range");
+  unsigned long long id = 0;
   std::lock_guard<std::mutex> lk(g_noalloc_mu);
-  if (!g_noalloc_ptr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess || !p)
-      return noalloc_fail(PGVIMP_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-    g_noalloc_ptr[dev] = static_cast<double*>(p);
-  }
-  *out = g_noalloc_ptr[dev];
+  pgvimp_status st = current_ctx_id(&id);
+  if (st != PGVIMP_OK) return st;
+  for (int k = 0; k < g_noalloc_used; ++k)
+    if (g_noalloc_cache[k].dev == dev && g_noalloc_cache[k].ctx_id == id) {
+      *out = g_noalloc_cache[k].ptr;
+      return PGVIMP_OK;
+    }
+  void* p = nullptr;
+  e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess || !p)
+    return noalloc_fail(PGVIMP_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+  NoallocEntry& slot = g_noalloc_cache[g_noalloc_used < kMaxEntries ? g_noalloc_used++ : g_noalloc_next];
+  if (g_noalloc_used == kMaxEntries) g_noalloc_next = (g_noalloc_next + 1) % kMaxEntries;
+  slot.dev = dev;
+  slot.ctx_id = id;
+  slot.ptr = static_cast<double*>(p);
+  *out = slot.ptr;
   return PGVIMP_OK;
 }
 

@@ -17,6 +17,7 @@ constexpr int kMaxSpheres = 64;
 constexpr int kMaxGH = 10;       // largest points-per-dimension of the GH rule
 constexpr int kScal = 24;        // per-plan scalar slots
 constexpr int kCrMaxThreads = 256; // largest thread block of the block (latency) form
+constexpr int kLaneThreads = 16;   // plan_threads value of the lane form (sixteen lanes per plan, n = 4)
 
 // Per-plan scalar slots (doubles).
 enum ScalSlot {
@@ -57,6 +58,7 @@ struct PlanDesc {
   int n, m, N, nq, dc;
   double T, dt;
   int rule, gh_p, max_bisect, iters, slr_iters, init_kind;
+  int update;                  // pgvimp_update: Thm 1 step or natural-gradient step
   double beta_max, kl_eps, init_scale;
   // cost
   int cost_kind, psi_form, factor_set;

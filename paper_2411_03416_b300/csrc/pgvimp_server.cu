@@ -6,7 +6,8 @@
 // a batch as soon as a launch slot, device memory and pinned staging are
 // free, and launches the whole plan (upload, prior, iterations, result download) on one of
 // several streams, so that batches admitted while others run overlap on the
-// GPU.  A stream callback hands the finished batch back to the scheduler,
+// GPU; each batch's launch sequence is captured into a CUDA graph and launched
+// as one.  A stream callback hands the finished batch back to the scheduler,
 // which copies each plan's result out, frees the batch's memory and admits
 // the next requests.  Device memory and pinned host staging come from two
 // pools allocated once at creation (first-fit with coalescing), so the
@@ -107,6 +108,7 @@ struct pgvimp_server {
   char* host_pool = nullptr;
   RangeAllocator dev_alloc, host_alloc;
   std::vector<cudaStream_t> streams;
+  std::vector<cudaGraphExec_t> execs;   // per stream slot: the last captured launch sequence
   std::vector<char> slot_busy;
   std::mutex mu;
   std::condition_variable cv_sched, cv_done;
@@ -117,6 +119,7 @@ struct pgvimp_server {
   bool stop = false;
   uint64_t next_id = 1;
   uint64_t launched_batches = 0, launched_plans = 0;
+  uint64_t graph_launches = 0, graph_instantiations = 0;   // batches launched as one graph; graphs built
   double host_launch_ms = 0.0, host_collect_ms = 0.0;   // scheduler time spent preparing / collecting batches
   std::thread worker;
   std::chrono::steady_clock::time_point t0;
@@ -166,12 +169,54 @@ pgvimp_status launch_flight(pgvimp_server* S, Flight* f) {
                                          S->host_pool + f->hout_off, &f->b, false);
   if (st != PGVIMP_OK) return st;
   void* s = S->streams[f->slot];
-  if ((st = pgvimp_batch_upload(f->b, s)) || (st = pgvimp_batch_reset(f->b, s)) || (st = pgvimp_batch_run(f->b, 0, s)) ||
-      (st = pgvimp_batch_download_results(f->b, s)))
-    return st;
-  cudaError_t e = cudaLaunchHostFunc(static_cast<cudaStream_t>(s), on_flight_done, f);
-  if (e != cudaSuccess) return server_fail(PGVIMP_ECUDA, std::string("cudaLaunchHostFunc: ") + cudaGetErrorString(e));
-  return PGVIMP_OK;
+  cudaStream_t cs = static_cast<cudaStream_t>(s);
+  auto enqueue = [&]() -> pgvimp_status {
+    pgvimp_status q;
+    if ((q = pgvimp_batch_upload(f->b, s)) || (q = pgvimp_batch_reset(f->b, s)) || (q = pgvimp_batch_run(f->b, 0, s)) ||
+        (q = pgvimp_batch_download_results(f->b, s)))
+      return q;
+    cudaError_t e = cudaLaunchHostFunc(cs, on_flight_done, f);
+    if (e != cudaSuccess) return server_fail(PGVIMP_ECUDA, std::string("cudaLaunchHostFunc: ") + cudaGetErrorString(e));
+    return PGVIMP_OK;
+  };
+  // The flight's whole launch sequence (copy in, prior, iterations, copy out,
+  // completion callback) is captured into a graph and launched as one.  The
+  // slot's executable graph is updated in place when the sequence has the same
+  // shape as the slot's last one (same kernels, new arena and argument values)
+  // and instantiated anew otherwise; the slot is idle while it is updated.
+  cudaGraph_t g = nullptr;
+  if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+    st = enqueue();
+    cudaError_t ec = cudaStreamEndCapture(cs, &g);
+    if (st != PGVIMP_OK) {
+      if (g) cudaGraphDestroy(g);
+      return st;
+    }
+    cudaGraphExec_t& ex = S->execs[f->slot];
+    if (ec == cudaSuccess && g) {
+      if (ex) {
+        cudaGraphExecUpdateResultInfo info;
+        if (cudaGraphExecUpdate(ex, g, &info) != cudaSuccess) {
+          cudaGetLastError();   // a shape change: build a new executable graph
+          cudaGraphExecDestroy(ex);
+          ex = nullptr;
+        }
+      }
+      if (!ex && cudaGraphInstantiate(&ex, g, 0) == cudaSuccess) ++S->graph_instantiations;
+      cudaGraphDestroy(g);
+      if (ex && cudaGraphLaunch(ex, cs) == cudaSuccess) {
+        ++S->graph_launches;
+        return PGVIMP_OK;
+      }
+    } else if (g) {
+      cudaGraphDestroy(g);
+    }
+    cudaGetLastError();
+  } else {
+    cudaGetLastError();
+  }
+  // capture, instantiation or graph launch unavailable: launch the sequence directly
+  return enqueue();
 }
 
 // Copies each plan's result out of a finished flight (scheduler thread, no
@@ -360,9 +405,9 @@ extern "C" pgvimp_status pgvimp_server_create(const pgvimp_server_config* cfg, p
   if (c.hbm_budget_bytes < ((size_t)1 << 20)) return server_fail(PGVIMP_EINVAL, "hbm_budget_bytes must be >= 1 MiB");
   if (c.max_inflight < 1 || c.max_inflight > 64) return server_fail(PGVIMP_EINVAL, "max_inflight must be in 1..64");
   if (c.max_batch < 1 || c.max_batch > (1 << 20)) return server_fail(PGVIMP_EINVAL, "max_batch must be >= 1");
-  if (c.plan_threads < -1 || (c.plan_threads > 1 && (c.plan_threads < 32 || c.plan_threads > kCrMaxThreads ||
-                                                      (c.plan_threads & 31))))
-    return server_fail(PGVIMP_EINVAL, "plan_threads must be -1, 0, 1, or a multiple of 32 in 32..256");
+  if (c.plan_threads < -1 || (c.plan_threads > 1 && c.plan_threads != kLaneThreads &&
+                              (c.plan_threads < 32 || c.plan_threads > kCrMaxThreads || (c.plan_threads & 31))))
+    return server_fail(PGVIMP_EINVAL, "plan_threads must be -1, 0, 1, 16, or a multiple of 32 in 32..256");
   if (!(c.batch_window_ms >= 0.0) || !(c.batch_window_ms < 1e7)) return server_fail(PGVIMP_EINVAL, "bad batch_window_ms");
   if (c.host_staging_bytes == 0) c.host_staging_bytes = std::min<size_t>(c.hbm_budget_bytes, (size_t)4 << 30);
   pgvimp_server* S = new (std::nothrow) pgvimp_server();
@@ -396,6 +441,7 @@ extern "C" pgvimp_status pgvimp_server_create(const pgvimp_server_config* cfg, p
     S->streams.push_back(s);
   }
   S->slot_busy.assign(c.max_inflight, 0);
+  S->execs.assign(c.max_inflight, nullptr);
   S->worker = std::thread(scheduler, S);
   *out = S;
   return PGVIMP_OK;
@@ -406,7 +452,6 @@ extern "C" pgvimp_status pgvimp_submit(pgvimp_server* S, const pgvimp_problem* p
   if (!S || !problem || !options || !request_id) return server_fail(PGVIMP_EINVAL, "NULL argument");
   pgvimp_options o = *options;
   if (S->cfg.plan_threads >= 0) o.plan_threads = S->cfg.plan_threads;
-  if (o.plan_threads == 1) o.plan_threads = 0;
   BatchSizes sz;
   pgvimp_status st = batch_sizes(1, problem, &o, S->cfg.precision, &sz);   // validates the request
   if (st != PGVIMP_OK) return st;
@@ -479,6 +524,8 @@ extern "C" pgvimp_status pgvimp_server_stats(pgvimp_server* S, pgvimp_server_sta
   out->now_ms = S->now_ms();
   out->host_launch_ms = S->host_launch_ms;
   out->host_collect_ms = S->host_collect_ms;
+  out->graph_launches = S->graph_launches;
+  out->graph_instantiations = S->graph_instantiations;
   return PGVIMP_OK;
 }
 
@@ -491,6 +538,8 @@ extern "C" pgvimp_status pgvimp_server_destroy(pgvimp_server* S) {
   }
   if (S->worker.joinable()) S->worker.join();   // returns once no batch is on the device
   for (auto& kv : S->reqs) delete kv.second;
+  for (cudaGraphExec_t ex : S->execs)
+    if (ex) cudaGraphExecDestroy(ex);
   for (cudaStream_t s : S->streams) cudaStreamDestroy(s);
   if (S->host_pool) cudaFreeHost(S->host_pool);
   if (S->dev_pool) cudaFree(S->dev_pool);

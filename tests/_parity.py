@@ -56,6 +56,40 @@ TIE_MIXED = dict(kl=1e-5, pd=1e-5)
 TIE_FP64 = dict(kl=1e-9, pd=1e-10)
 
 
+_KAPPA = {}
+
+
+def prior_condition(pb):
+    """2-norm condition number of the prior precision K^-1 (cached per
+    problem shape)."""
+    key = (pb.n, pb.N, pb.T, pb.dyn_kind, np.asarray(pb.Qc).tobytes(), np.asarray(pb.K0).tobytes(),
+           np.asarray(pb.KN).tobytes(), np.asarray(pb.A).tobytes())
+    if key not in _KAPPA:
+        pr = oracle.prior(pb)
+        n, N = pb.n, pb.N
+        D = n * (N + 1)
+        M = np.zeros((D, D))
+        for i in range(N + 1):
+            M[i * n:(i + 1) * n, i * n:(i + 1) * n] = pr.Kd[i]
+        for i in range(N):
+            M[(i + 1) * n:(i + 2) * n, i * n:(i + 1) * n] = pr.Ko[i]
+            M[i * n:(i + 1) * n, (i + 1) * n:(i + 2) * n] = pr.Ko[i].T
+        _KAPPA[key] = float(np.linalg.cond(M))
+    return _KAPPA[key]
+
+
+def tie_from_conditioning(pb, prec):
+    """Tie margins for a precision form: the fixed margins above, or ten times
+    kappa(K^-1) times the unit roundoff of the recursions (2^-53 in FP64,
+    2^-48 in double-float) where that is larger -- the size by which two
+    correct eliminations of the chain can differ.  For the 750-step robot
+    (kappa 4.7e10) this is 1.7e-3 in double-float and 5.2e-5 in FP64."""
+    base = TIE_FP64 if prec == 0 else TIE_MIXED
+    u = 2.0 ** -48 if prec == 2 else 2.0 ** -53
+    floor = 10.0 * prior_condition(pb) * u
+    return dict(kl=max(base["kl"], floor), pd=max(base["pd"], floor))
+
+
 def gpu_solve(problems, options, precision):
     import paper_2411_03416_b300 as pg
     return pg.solve(problems, options, precision)
@@ -121,14 +155,18 @@ def check_tie_replays(ora, gbetas, glogs, op, tie):
     return out
 
 
-def compare_plan(pb, op, gres, *, rtol_mu, rtol_sigma, tie=None, max_replays=None, slr=False):
+def compare_plan(pb, op, gres, *, rtol_mu, rtol_sigma, tie=None, prec=None, max_replays=None, slr=False):
     """Compares one GPU plan with the oracle.  If the accepted step sizes
     differ, the oracle is rerun replaying the GPU's steps, and every decision
     that differs must be a tie of the step-size search (check_tie_replays).
-    `tie` defaults to TIE_MIXED when the tolerances are mixed-precision ones,
-    else TIE_FP64; `max_replays` bounds the replayed decisions."""
+    `tie` defaults to tie_from_conditioning(pb, prec) when the precision form
+    is given, else to TIE_MIXED for mixed-precision tolerances and TIE_FP64
+    otherwise; `max_replays` bounds the replayed decisions."""
     if tie is None:
-        tie = TIE_MIXED if rtol_mu >= 1e-6 else TIE_FP64
+        if prec is not None:
+            tie = tie_from_conditioning(pb, prec)
+        else:
+            tie = TIE_MIXED if rtol_mu >= 1e-6 else TIE_FP64
     ora = oracle_solve(pb, op)
     gb = np.array([l["beta"] for l in gres.logs])
     ob = np.array([l["beta"] for l in ora.logs])

@@ -11,13 +11,15 @@
 //   1/sqrt (one Newton step)    |err| <= 16 u^2 / sqrt(v)   (the host starts from a correctly
 //                                 rounded 1/sqrtf, the device from rsqrtf: the refinement is checked)
 //   log det accumulator         |err| <= 16 u^2 * count in the log
+//   reciprocal (one Newton step) |err| <= 8 u^2 / |v|
+//   four-term dot product       |err| <= 16 u^2 sum_t |x_t y_t|   (compensated, no cancellation bound)
 // Prints the largest observed error over its bound per operation, then "ok"
 // when every ratio is at most 1.
 #include <cmath>
 #include <cstdio>
 #include <random>
 
-#include "pgvimp_device.cuh"
+#include "pgvimp_dfx.cuh"
 
 using pgv::df64;
 
@@ -45,7 +47,8 @@ int main() {
     const double v = std::ldexp(mant(rng), (int)std::floor(expo(rng)));
     return coin(rng) < 0.5 ? -v : v;
   };
-  Worst conv{"conversion"}, mul{"product"}, add{"sum"}, fma{"fused"}, rs{"rsqrt"}, ld{"logdet"};
+  Worst conv{"conversion"}, mul{"product"}, add{"sum"}, fma{"fused"}, rs{"rsqrt"}, ld{"logdet"}, rc{"reciprocal"},
+      dot{"dot4"};
   for (int t = 0; t < 200000; ++t) {
     const double a = draw(), b = draw(), c = draw();
     const df64 x = pgv::r_from<df64>(a), y = pgv::r_from<df64>(b), z = pgv::r_from<df64>(c);
@@ -57,6 +60,31 @@ int main() {
     const df64 p = pgv::r_from<df64>(std::fabs(a));
     const long double P = exact(p);
     rs.see(exact(pgv::r_rsqrt(p)) - 1.0L / std::sqrt(P), 16 * kU2 / std::sqrt(P));
+    rc.see(exact(pgv::df_rcp(x)) - 1.0L / X, 8 * kU2 / std::fabs(X));
+    df64 u[4], v[4];
+    long double want = 0.0L, mag = 0.0L;
+    for (int k = 0; k < 4; ++k) {
+      u[k] = pgv::r_from<df64>(draw());
+      v[k] = pgv::r_from<df64>(draw());
+      want += exact(u[k]) * exact(v[k]);
+      mag += std::fabs(exact(u[k]) * exact(v[k]));
+    }
+    dot.see(exact(pgv::df_dot4(u, v)) - want, 16 * kU2 * mag);
+  }
+  // dot products that nearly cancel
+  for (int t = 0; t < 50000; ++t) {
+    df64 u[4], v[4];
+    const double a = draw(), b = draw(), d = std::ldexp(mant(rng), -(int)(20 + 20 * coin(rng)));
+    u[0] = pgv::r_from<df64>(a); v[0] = pgv::r_from<df64>(b);
+    u[1] = pgv::r_from<df64>(-a); v[1] = pgv::r_from<df64>(b * (1.0 + d));
+    u[2] = pgv::r_from<df64>(draw() * 1e-3); v[2] = pgv::r_from<df64>(draw());
+    u[3] = pgv::r_from<df64>(draw()); v[3] = pgv::r_from<df64>(draw() * 1e-3);
+    long double want = 0.0L, mag = 0.0L;
+    for (int k = 0; k < 4; ++k) {
+      want += exact(u[k]) * exact(v[k]);
+      mag += std::fabs(exact(u[k]) * exact(v[k]));
+    }
+    dot.see(exact(pgv::df_dot4(u, v)) - want, 16 * kU2 * mag);
   }
   // sums and fused sums that nearly cancel: y = -x (1 + d), |d| down to 2^-40
   for (int t = 0; t < 50000; ++t) {
@@ -82,7 +110,7 @@ int main() {
     ld.see((long double)acc.log_value() - want, 16 * kU2 * count + 1e-15L * std::fabs(want));
   }
   bool ok = true;
-  for (const Worst* w : {&conv, &mul, &add, &fma, &rs, &ld}) {
+  for (const Worst* w : {&conv, &mul, &add, &fma, &rs, &ld, &rc, &dot}) {
     std::printf("%s %.3f\n", w->name, w->ratio);
     ok = ok && w->ratio <= 1.0;
   }

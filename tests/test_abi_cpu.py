@@ -113,21 +113,36 @@ def test_plans_sharing_a_map_store_it_once(pg):
 
 
 def test_plan_threads_validation(pg):
-    """The block form takes 32..256 threads in multiples of 32, one value per batch."""
+    """The thread form (1), the lane form (16, n = 4 only), the default (0) and
+    the block form with 32..256 threads in multiples of 32; one value per batch."""
     from paper_2411_03416_b300 import _lib
     pb, op = W.c1_point2d()
-    for bad in (-1, 2, 48, 288, 512):
+    for bad in (-1, 2, 8, 48, 288, 512):
         assert _arena_status(pg, pb, replace(op, plan_threads=bad))[0] == _lib.EINVAL
-    for good in (0, 1, 32, 64, 256):
+    for good in (0, 1, 16, 32, 64, 256):
         assert _arena_status(pg, pb, replace(op, plan_threads=good))[0] == 0
+    pq, oq = W.c4_quadrotor(N=20)
+    assert _arena_status(pg, pq, replace(oq, plan_threads=16))[0] == _lib.EINVAL
     keep = _lib._Keep()
     parr = (_lib.Problem * 2)(*[_lib.marshal_problem(pb, keep) for _ in range(2)])
-    oarr = (_lib.Options * 2)(_lib.marshal_options(op), _lib.marshal_options(replace(op, plan_threads=64)))
+    oarr = (_lib.Options * 2)(_lib.marshal_options(op), _lib.marshal_options(replace(op, plan_threads=16)))
     nb = C.c_size_t(0)
     st = pg.lib().pgvimp_batch_arena_bytes(2, C.cast(parr, C.c_void_p), C.cast(oarr, C.c_void_p), 1, C.byref(nb))
     assert st == _lib.EINVAL
-    # the block form runs FP64 or mixed recursions, not double-float
-    assert _arena_status(pg, pb, replace(op, plan_threads=64), precision=2)[0] == _lib.EINVAL
+    # the block form runs every precision, double-float recursions included
+    assert _arena_status(pg, pb, replace(op, plan_threads=64), precision=2)[0] == 0
+
+
+def test_update_validation(pg):
+    """The update is Thm 1's (0) or the natural-gradient step (1), which
+    needs beta_max <= 1."""
+    from paper_2411_03416_b300 import _lib
+    pb, op = W.c1_point2d()
+    assert _arena_status(pg, pb, replace(op, update=1))[0] == 0
+    assert _arena_status(pg, pb, replace(op, update=2))[0] == _lib.EINVAL
+    assert _arena_status(pg, pb, replace(op, update=-1))[0] == _lib.EINVAL
+    assert _arena_status(pg, pb, replace(op, update=1, beta_max=1.5))[0] == _lib.EINVAL
+    assert _arena_status(pg, pb, replace(op, update=0, beta_max=1.5))[0] == 0
 
 
 def test_temperature_schedule_validation(pg):

@@ -28,11 +28,11 @@ def block(op, tpb=64):
     return replace(op, plan_threads=tpb)
 
 
-@pytest.mark.parametrize("prec,tol", [(FP64, TOL_FP64_SMALL), (MIXED, TOL_MIXED)])
+@pytest.mark.parametrize("prec,tol", [(FP64, TOL_FP64_SMALL), (MIXED, TOL_MIXED), (MIXED_DF, TOL_MIXED)])
 def test_c1_point2d_block_form(pg, prec, tol):
     pb, op = W.c1_point2d()
     res = gpu_solve([pb], [block(op)], prec)[0]
-    compare_plan(pb, op, res, rtol_mu=tol["mu"], rtol_sigma=tol["sigma"])
+    compare_plan(pb, op, res, rtol_mu=tol["mu"], rtol_sigma=tol["sigma"], prec=prec)
     assert len(res.logs) == op.iters
 
 
@@ -48,11 +48,11 @@ def test_reduction_levels_fp64(pg, N, tpb):
     compare_plan(pb, op, res, rtol_mu=tol, rtol_sigma=tol)
 
 
-@pytest.mark.parametrize("prec,tol", [(FP64, TOL_FP64_SMALL), (MIXED, TOL_MIXED)])
+@pytest.mark.parametrize("prec,tol", [(FP64, TOL_FP64_SMALL), (MIXED, TOL_MIXED), (MIXED_DF, TOL_MIXED)])
 def test_c3_arm_block_form(pg, prec, tol):
     pb, op = W.c3_arm(N=30, iters=10)
     res = gpu_solve([pb], [block(op, 32)], prec)[0]
-    compare_plan(pb, op, res, rtol_mu=tol["mu"], rtol_sigma=tol["sigma"])
+    compare_plan(pb, op, res, rtol_mu=tol["mu"], rtol_sigma=tol["sigma"], prec=prec)
 
 
 def test_c4_quadrotor_slr_block_form_fp64(pg):
@@ -75,7 +75,7 @@ def test_c4_quadrotor_first_linearisation_block_form_mixed(pg, N):
 def test_c2_dense_horizon_block_form_first_iterations(pg, prec, tol, iters):
     pb, op = W.c2_point2d_dense(iters=iters)
     res = gpu_solve([pb], [block(op, 128)], prec)[0]
-    compare_plan(pb, op, res, rtol_mu=tol["mu"], rtol_sigma=tol["sigma"])
+    compare_plan(pb, op, res, rtol_mu=tol["mu"], rtol_sigma=tol["sigma"], prec=prec)
 
 
 def test_block_form_matches_thread_form(pg):
@@ -122,3 +122,35 @@ def test_c2_full_plan_invariants_block_form(pg):
             k = l["beta"] / op.beta_max * 2 ** op.max_bisect
             assert abs(k - round(k)) < 1e-9
     assert res.logs[-1]["collision_cost"] < res.logs[0]["collision_cost"]
+
+
+@pytest.mark.parametrize("N", [1, 2, 7, 8, 9, 33, 100])
+@pytest.mark.parametrize("tpb", [32, 128])
+def test_reduction_levels_double_float(pg, N, tpb):
+    """The block form with double-float recursions over the level structures
+    of the cyclic reduction (a binding KL bound runs several trials)."""
+    pb, op = W.c1_point2d(N=N, iters=4)
+    op = replace(op, kl_eps=0.05 * (N + 1))
+    res = gpu_solve([pb], [block(op, tpb)], MIXED_DF)[0]
+    compare_plan(pb, op, res, rtol_mu=TOL_MIXED["mu"], rtol_sigma=TOL_MIXED["sigma"], prec=MIXED_DF)
+
+
+@pytest.mark.parametrize("n_make", ["point3d", "quadrotor"])
+def test_double_float_block_form_other_dimensions(pg, n_make):
+    """n = 6: the 3-D point robot and the first linearisation of Alg. 2."""
+    if n_make == "point3d":
+        pb, op = W.point3d(request=1, N=80)
+    else:
+        pb, op = W.c4_quadrotor(N=60, iters=3, slr_iters=1)
+    res = gpu_solve([pb], [block(op, 64)], MIXED_DF)[0]
+    compare_plan(pb, op, res, rtol_mu=TOL_MIXED["mu"], rtol_sigma=TOL_MIXED["sigma"], prec=MIXED_DF)
+
+
+def test_double_float_block_form_equals_alone_in_a_batch(pg):
+    probs = [W.c1_point2d(request=r, N=N, iters=6) for r, N in enumerate([7, 50, 33, 1])]
+    pbs, ops = [p for p, _ in probs], [block(o, 64) for _, o in probs]
+    together = gpu_solve(pbs, ops, MIXED_DF)
+    for i in range(len(probs)):
+        alone = gpu_solve([pbs[i]], [ops[i]], MIXED_DF)[0]
+        np.testing.assert_array_equal(together[i].mu, alone.mu)
+        np.testing.assert_array_equal(together[i].Sd, alone.Sd)

@@ -28,7 +28,8 @@ def pg():
 def test_c1_point2d(pg, prec, tol):
     pb, op = W.c1_point2d()
     res = gpu_solve([pb], [op], prec)[0]
-    info, ora = compare_plan(pb, op, res, rtol_mu=tol["mu"], rtol_sigma=tol["sigma"])
+    info, ora = compare_plan(pb, op, res, rtol_mu=tol["mu"], rtol_sigma=tol["sigma"],
+                             max_replays=0 if prec == FP64 else None, prec=prec)
     assert len(res.logs) == op.iters
     # logged costs follow the oracle's
     for lg, lo in zip(res.logs, ora.logs):
@@ -36,20 +37,55 @@ def test_c1_point2d(pg, prec, tol):
         assert abs(lg["entropy"] - lo["entropy"]) <= 1e-6 * abs(lo["entropy"])
 
 
+# The throughput forms of n = 4: one thread per plan (1) and sixteen lanes per
+# plan (16, the default with double-float recursions), in every precision.
+@pytest.mark.parametrize("form", [1, 16])
+@pytest.mark.parametrize("prec,tol", [(FP64, TOL_FP64_SMALL), (MIXED, TOL_MIXED), (MIXED_DF, TOL_MIXED)])
+def test_c1_point2d_thread_and_lane_forms(pg, prec, tol, form):
+    pb, op = W.c1_point2d()
+    res = gpu_solve([pb], [replace(op, plan_threads=form)], prec)[0]
+    compare_plan(pb, op, res, rtol_mu=tol["mu"], rtol_sigma=tol["sigma"], max_replays=0 if prec == FP64 else None, prec=prec)
+
+
+@pytest.mark.parametrize("form", [1, 16])
+def test_binding_kl_bound_thread_and_lane_forms_fp64(pg, form):
+    pb, op = W.c1_point2d(N=33, iters=8)
+    op = replace(op, kl_eps=0.4)
+    res = gpu_solve([pb], [replace(op, plan_threads=form)], FP64)[0]
+    assert any(l["trials"] > 1 for l in res.logs)
+    compare_plan(pb, op, res, rtol_mu=1e-9, rtol_sigma=1e-9, max_replays=0)
+
+
+@pytest.mark.parametrize("form", [1, 16])
+def test_dense_horizon_first_iterations_thread_and_lane_forms(pg, form):
+    pb, op = W.c2_point2d_dense(iters=2)
+    res = gpu_solve([pb], [replace(op, plan_threads=form)], MIXED_DF)[0]
+    compare_plan(pb, op, res, rtol_mu=TOL_MIXED["mu"], rtol_sigma=TOL_MIXED["sigma"], prec=MIXED_DF)
+
+
 # At N = 750 the iteration is chaotic in FP64: the oracle against itself with a
-# 1e-12 relative change of the goal (same step sequence) differs in the mean by
-# 1.7e-7 after one iteration, 5e-7 after three, 7e-2 after six and 0.27 after
-# thirty, and in the marginal covariances by 3.8e-7, 2.1e-6 and 5.0e-4 after
-# one, two and three iterations.
-# Whole-plan agreement is therefore bounded by that divergence; the full-size
-# parity runs the first iterations, and the whole plan is checked through
-# properties that hold at any size.
+# 1e-12 relative change of the goal (same step sequence) differs after
+# k = 1, 2, 3, 4, 5, 6, 8 iterations by
+#   mean:                 1.7e-7, 1.5e-7, 5.0e-7, 5.5e-5, 2.5e-5, 2.4e-4, 0.11
+#   marginal covariances: 3.8e-7, 2.1e-6, 5.0e-4, 2.9e-4, 5.5e-3, 0.18,   1.9
+# (its own step choice first moves at k = 6).  Whole-plan agreement is
+# therefore bounded by that divergence.  The full-size parity compares every
+# iteration count whose self-divergence stays below a tenth of the tolerance:
+# k = 1, 2 for the covariances (1e-4 for the mixed forms), k = 3 as well for
+# the FP64 mean, whose covariance bound there is twice the measured 5.0e-4;
+# the whole plan is checked through properties that hold at any size.
 @pytest.mark.parametrize("iters", [1, 2])
 @pytest.mark.parametrize("prec,tol", [(FP64, dict(mu=1e-5, sigma=1e-5)), (MIXED, TOL_MIXED), (MIXED_DF, TOL_MIXED)])
 def test_c2_dense_horizon_full_size_first_iterations(pg, prec, tol, iters):
     pb, op = W.c2_point2d_dense(iters=iters)
     res = gpu_solve([pb], [op], prec)[0]
-    compare_plan(pb, op, res, rtol_mu=tol["mu"], rtol_sigma=tol["sigma"])
+    compare_plan(pb, op, res, rtol_mu=tol["mu"], rtol_sigma=tol["sigma"], prec=prec)
+
+
+def test_c2_dense_horizon_full_size_three_iterations_fp64(pg):
+    pb, op = W.c2_point2d_dense(iters=3)
+    res = gpu_solve([pb], [op], FP64)[0]
+    compare_plan(pb, op, res, rtol_mu=1e-5, rtol_sigma=1e-3, prec=FP64)
 
 
 def _check_plan_invariants(pb, op, res):
@@ -78,14 +114,27 @@ def test_c2_dense_horizon_full_plan_invariants(pg, prec):
 def test_c3_arm_short(pg, prec, tol):
     pb, op = W.c3_arm(N=30, iters=10)
     res = gpu_solve([pb], [op], prec)[0]
-    compare_plan(pb, op, res, rtol_mu=tol["mu"], rtol_sigma=tol["sigma"])
+    compare_plan(pb, op, res, rtol_mu=tol["mu"], rtol_sigma=tol["sigma"], prec=prec)
 
 
 @pytest.mark.parametrize("prec", [MIXED, MIXED_DF])
 def test_c3_arm_full_size(pg, prec):
     pb, op = W.c3_arm()
     res = gpu_solve([pb], [op], prec)[0]
-    compare_plan(pb, op, res, rtol_mu=TOL_MIXED["mu"], rtol_sigma=TOL_MIXED["sigma"])
+    compare_plan(pb, op, res, rtol_mu=TOL_MIXED["mu"], rtol_sigma=TOL_MIXED["sigma"], prec=prec)
+
+
+# The arm plan is not chaotic but ill-conditioned at the rounding level: the
+# FP64 oracle against the same source built with FMA contraction (every
+# a*b+c rounded once instead of twice, the kind of difference two FP64
+# implementations have) differs after the 25 iterations by 9.4e-8 (mean) and
+# 5.8e-7 (covariances), with the same step sequence; a 1e-15 relative change
+# of sigma_obs moves it by 5e-9 / 3e-8.  The FP64 bound is ten times that
+# rounding floor.
+def test_c3_arm_full_size_fp64(pg):
+    pb, op = W.c3_arm()
+    res = gpu_solve([pb], [op], FP64)[0]
+    compare_plan(pb, op, res, rtol_mu=1e-6, rtol_sigma=6e-6, max_replays=0, prec=FP64)
 
 
 # Alg. 2 on the quadrotor is chaotic as well: at N = 40 (3 x 5 iterations) the
@@ -107,7 +156,7 @@ def test_c4_quadrotor_slr_short_fp64(pg):
 def test_c4_quadrotor_first_linearisation_mixed(pg, N, iters, prec):
     pb, op = W.c4_quadrotor(N=N, iters=iters, slr_iters=1)
     res = gpu_solve([pb], [op], prec)[0]
-    compare_plan(pb, op, res, rtol_mu=TOL_MIXED["mu"], rtol_sigma=TOL_MIXED["sigma"])
+    compare_plan(pb, op, res, rtol_mu=TOL_MIXED["mu"], rtol_sigma=TOL_MIXED["sigma"], prec=prec)
 
 
 @pytest.mark.parametrize("prec", [FP64, MIXED, MIXED_DF])
@@ -142,11 +191,11 @@ def test_binding_kl_bound_and_options(pg):
     op = replace(op, kl_eps=0.5)
     res = gpu_solve([pb], [op], FP64)[0]
     assert any(l["trials"] > 1 for l in res.logs)
-    compare_plan(pb, op, res, rtol_mu=1e-9, rtol_sigma=1e-9)
+    compare_plan(pb, op, res, rtol_mu=1e-9, rtol_sigma=1e-9, max_replays=0)
     pb2 = replace(pb, factor_set=1, psi_form=1, temperature=3.0)
     op2 = replace(op, init_kind=1, init_scale=50.0, kl_eps=0.1 * 31)
     res2 = gpu_solve([pb2], [op2], FP64)[0]
-    compare_plan(pb2, op2, res2, rtol_mu=1e-9, rtol_sigma=1e-9)
+    compare_plan(pb2, op2, res2, rtol_mu=1e-9, rtol_sigma=1e-9, max_replays=0)
 
 
 @pytest.mark.parametrize("prec", [MIXED, MIXED_DF])
@@ -228,7 +277,7 @@ def test_point3d_thread_form(pg, prec, tol):
     points on the three position coordinates (the oracle runs all 729)."""
     pb, op = W.point3d()
     res = gpu_solve([pb], [op], prec)[0]
-    compare_plan(pb, op, res, rtol_mu=tol["mu"], rtol_sigma=tol["sigma"])
+    compare_plan(pb, op, res, rtol_mu=tol["mu"], rtol_sigma=tol["sigma"], max_replays=0 if prec == FP64 else None, prec=prec)
     assert res.logs[-1]["collision_cost"] < res.logs[0]["collision_cost"]
 
 
@@ -236,7 +285,7 @@ def test_point3d_thread_form(pg, prec, tol):
 def test_point3d_block_form(pg, prec, tol):
     pb, op = W.point3d(request=1, N=80)
     res = gpu_solve([pb], [replace(op, plan_threads=64)], prec)[0]
-    compare_plan(pb, op, res, rtol_mu=tol["mu"], rtol_sigma=tol["sigma"])
+    compare_plan(pb, op, res, rtol_mu=tol["mu"], rtol_sigma=tol["sigma"], prec=prec)
 
 
 # ------------------------------------------------------- two-phase temperature
@@ -249,7 +298,7 @@ def test_two_phase_temperature(pg, prec, tol, tpb):
     pb, op = W.c1_point2d(N=40, iters=20)
     op = replace(op, temperature_high=10.0, switch_iter=10)
     res = gpu_solve([pb], [replace(op, plan_threads=tpb)], prec)[0]
-    compare_plan(pb, op, res, rtol_mu=tol["mu"], rtol_sigma=tol["sigma"])
+    compare_plan(pb, op, res, rtol_mu=tol["mu"], rtol_sigma=tol["sigma"], prec=prec)
     ent = [l["entropy"] for l in res.logs]
     assert ent[-1] > ent[9] + 1.0                   # the high temperature favours entropy
 
@@ -274,7 +323,7 @@ def test_smolyak_point2d(pg, prec, tol, tpb):
     pb, op = W.c1_point2d(N=40, iters=10)
     op = replace(op, rule=W.RULE_SMOLYAK, gh_p=3)
     res = gpu_solve([pb], [replace(op, plan_threads=tpb)], prec)[0]
-    compare_plan(pb, op, res, rtol_mu=tol["mu"], rtol_sigma=tol["sigma"])
+    compare_plan(pb, op, res, rtol_mu=tol["mu"], rtol_sigma=tol["sigma"], max_replays=0 if prec == FP64 else None, prec=prec)
 
 
 @pytest.mark.parametrize("k", [2, 3])
@@ -285,7 +334,7 @@ def test_smolyak_arm(pg, k, prec, tol):
     pb, op = W.c3_arm(N=24, iters=6)
     op = replace(op, rule=W.RULE_SMOLYAK, gh_p=k)
     res = gpu_solve([pb], [op], prec)[0]
-    compare_plan(pb, op, res, rtol_mu=tol["mu"], rtol_sigma=tol["sigma"])
+    compare_plan(pb, op, res, rtol_mu=tol["mu"], rtol_sigma=tol["sigma"], prec=prec)
 
 
 @pytest.mark.parametrize("tpb", [0, 64])

@@ -150,14 +150,16 @@ def test_marginals_not_pd_sets_status(pg):
 
 # --------------------------------------------------------- a2-a4 quadrature
 
-def _oracle_grads(pb, op, mu, Sd):
+def _oracle_grads(pb, op, mu, Sd, per_factor=False):
     n = pb.n
     g, G, coll = np.zeros_like(mu), np.zeros_like(Sd), 0.0
+    s0 = np.zeros(pb.N + 1)
     for i in range(pb.N + 1):
         S0, S1, S2 = oracle.quad_moments(pb, op, i, mu[i], Sd[i])
         g[i], G[i] = oracle.gradients(Sd[i], S0, S1, S2)
         coll += S0
-    return g, G, coll
+        s0[i] = S0
+    return (g, G, coll, s0) if per_factor else (g, G, coll)
 
 
 CASES = [
@@ -192,7 +194,7 @@ def test_quadrature_and_gradients(pg, name, make, prec):
     b.write(0, pg.BUF_SD, Sd)
     b.phase(pg.PHASE_QUAD)
     _sync()
-    g_o, G_o, coll_o = _oracle_grads(pb, op, mu, Sd)
+    g_o, G_o, coll_o, s0_o = _oracle_grads(pb, op, mu, Sd, per_factor=True)
     g = b.read(0, pg.BUF_G1, g_o.shape)
     G = b.read(0, pg.BUF_G2, G_o.shape)
     coll = b.read(0, pg.BUF_SCAL, (24,))[pg.S_COLL]
@@ -201,6 +203,21 @@ def test_quadrature_and_gradients(pg, name, make, prec):
     assert abs(coll - coll_o) <= tol * abs(coll_o) + 1e-12
     assert rel(g, g_o) <= tol, (rel(g, g_o), name)
     assert rel(G, G_o) <= tol, (rel(G, G_o), name)
+    # factor by factor, wherever the hinge is active: a wrong factor near the
+    # start or goal, where psi is small, cannot hide in the whole-array norm
+    active = np.nonzero(s0_o > 1e-6 * s0_o.max())[0]
+    assert len(active) >= 2
+    ftol = 1e-8 if prec == FP64 else 2e-3
+    worst = []
+    for i in active:
+        eg = np.linalg.norm(g[i] - g_o[i]) / np.linalg.norm(g_o[i])
+        eG = np.linalg.norm(G[i] - G_o[i]) / np.linalg.norm(G_o[i])
+        worst.append((max(eg, eG), i))
+        assert eg <= ftol and eG <= ftol, (name, i, s0_o[i], eg, eG)
+    # in FP64, factors with no active sigma point are exactly zero on both sides
+    if prec == FP64:
+        inactive = np.nonzero(s0_o == 0.0)[0]
+        assert np.all(g[inactive] == 0.0) and np.all(G[inactive] == 0.0), name
     b.close()
 
 

@@ -36,8 +36,10 @@ def _mix():
     return reqs
 
 
-@pytest.mark.parametrize("prec,tpb", [(MIXED, 64), (MIXED_DF, 0), (MIXED, 0), (FP64, 32)])
+@pytest.mark.parametrize("prec,tpb", [(MIXED, 64), (MIXED_DF, 0), (MIXED, 0), (FP64, 32), (MIXED_DF, 64)])
 def test_server_results_equal_alone(pg, prec, tpb):
+    """Every batch is launched as one captured CUDA graph; each result equals
+    the same plan run alone."""
     reqs = _mix()
     srv = pg.Server(2 << 30, precision=prec, plan_threads=tpb, max_inflight=4, max_batch=8, batch_window_ms=5.0)
     ids = [srv.submit(pb, op) for pb, op in reqs]
@@ -46,6 +48,7 @@ def test_server_results_equal_alone(pg, prec, tpb):
     srv.close()
     assert all(o is not None for o in out)
     assert stats["plans"] == len(reqs)
+    assert stats["graph_launches"] == stats["batches"] and stats["graph_instantiations"] >= 1
     for (pb, op), (mu, Sd, info) in zip(reqs, out):
         alone = gpu_solve([pb], [replace(op, plan_threads=tpb)], prec)[0]
         np.testing.assert_array_equal(mu, alone.mu)

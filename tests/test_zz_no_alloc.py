@@ -4,12 +4,13 @@ It serves callers that cannot allocate device memory (for example while
 their stream is captured into a CUDA graph, or under a fixed memory budget):
 its scratch is a fixed device array inside the library.  Its results must
 equal those of the allocating path, PGVIMP_PHASE_MARGINALS on a batch, on two
-calls in a row (the second call reuses the shared scratch left by the first).
-This file is collected last so that a failure here comes after every other
-test has run."""
+calls in a row (the second call reuses the shared scratch left by the first),
+and the oracle's belief-propagation marginals.  This file is collected last
+so that a failure here comes after every other test has run."""
 import numpy as np
 import pytest
 
+import oracle
 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -68,6 +69,45 @@ def test_noalloc_marginals_match_allocating_path_twice(make, N):
         np.testing.assert_allclose(Sd, Sd_r, rtol=1e-12, atol=1e-14 * np.abs(Sd_r).max(), err_msg=f"call {call}")
         np.testing.assert_allclose(So, So_r, rtol=1e-12, atol=1e-14 * np.abs(So_r).max(), err_msg=f"call {call}")
         assert abs(ld - ld_r) <= 1e-12 * abs(ld_r), (call, ld, ld_r)
+        # and the oracle (literal GBP messages), element by element
+        Sd_o, So_o, ld_o = oracle.marginals(Ld, Lo)
+        np.testing.assert_allclose(Sd, Sd_o, rtol=1e-10, atol=1e-12 * np.abs(Sd_o).max(), err_msg=f"call {call}")
+        np.testing.assert_allclose(So, So_o, rtol=1e-10, atol=1e-12 * np.abs(So_o).max(), err_msg=f"call {call}")
+        assert abs(ld - ld_o) <= 1e-10 * abs(ld_o), (call, ld, ld_o)
+
+
+def _spd_chain_blocks(rng, n, N, scale):
+    """B^T B + I for a random block-bidiagonal B, assembled block by block
+    (large N without the dense matrix)."""
+    Bd = rng.standard_normal((N + 1, n, n)) + 2 * np.eye(n)
+    Bu = rng.standard_normal((N, n, n))        # block (i, i+1)
+    Ld = np.einsum("iab,iac->ibc", Bd, Bd) + np.eye(n)
+    Ld[1:] += np.einsum("iab,iac->ibc", Bu, Bu)
+    Lo = np.einsum("iab,iac->ibc", Bu, Bd[:-1])  # (B^T B)_{i+1,i} = B_{i,i+1}^T B_{i,i}
+    return scale * Ld, scale * Lo
+
+
+def test_noalloc_at_the_largest_accepted_size():
+    """n = 4 with N = 20163, the largest horizon the fixed 4 MiB scratch
+    holds, is accepted and matches the oracle; N = 20164 is rejected."""
+    import torch
+    from paper_2411_03416_b300 import _lib as L
+    n, N = 4, 20163
+    rng = np.random.default_rng(77)
+    Ld, Lo = _spd_chain_blocks(rng, n, N, 2.0)
+    Sd_t = torch.empty((N + 1, n, n), dtype=torch.float64, device="cuda")
+    So_t = torch.empty((N, n, n), dtype=torch.float64, device="cuda")
+    ld_t = torch.empty(1, dtype=torch.float64, device="cuda")
+    L.marginals_noalloc(n, N, torch.from_numpy(Ld).cuda(), torch.from_numpy(Lo).cuda(), Sd_t, So_t, ld_t)
+    torch.cuda.synchronize()
+    Sd_o, So_o, ld_o = oracle.marginals(Ld, Lo)
+    np.testing.assert_allclose(Sd_t.cpu().numpy(), Sd_o, rtol=1e-10, atol=1e-12 * np.abs(Sd_o).max())
+    np.testing.assert_allclose(So_t.cpu().numpy(), So_o, rtol=1e-10, atol=1e-12 * np.abs(So_o).max())
+    assert abs(float(ld_t.item()) - ld_o) <= 1e-10 * abs(ld_o)
+    t = torch.zeros(16, dtype=torch.float64, device="cuda")
+    with pytest.raises(L.PgvimpError) as e:
+        L.marginals_noalloc(n, N + 1, t, t, t, t, t)
+    assert e.value.status == L.EINVAL
 
 
 def test_noalloc_rejects_sizes_beyond_the_fixed_scratch():
