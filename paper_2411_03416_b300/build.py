@@ -24,12 +24,7 @@ SOURCES = ["pgvimp_api.cu", "pgvimp_noalloc.cu", "pgvimp_server.cu", "k4_lane_df
 HEADERS = ["pgvimp_device.cuh", "pgvimp_dfx.cuh", "pgvimp_kernels.cuh", "pgvimp_cr.cuh", "pgvimp_lane.cuh", "pgvimp_plan.h",
            "pgvimp_launch.h", "pgvimp_internal.h", "pgvimp_pool.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-# The block form with double-float recursions is built with the front-end
-# (NVVM) optimiser at -O1 (ptxas keeps -O3): at the default -O3 the root pivot
-# of its cyclic reduction was miscomputed for n = 4 (a stand-alone reduction of
-# a two-state chain fails at -O3 and is exact at -O1, at -O0 and with -G, and
-# exact at -O3 once a printf is added inside it).
-EXTRA_FLAGS = {f"k{n}_cta_df.cu": ["-Xcicc", "-O1"] for n in (4, 6, 14)}
+EXTRA_FLAGS = {}   # per-unit extra nvcc flags
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "-I", os.path.join(ROOT, "include")]
 
 

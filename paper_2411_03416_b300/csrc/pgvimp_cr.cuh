@@ -133,6 +133,15 @@ PGV_DEV void sub_mv(const R* X, const R* v, R* y, bool trans) {
   }
 }
 
+// The root's pivot block inverse, out of line.  (Inlined, the double-float
+// n = 4 build miscomputed the root pivot at the default front-end
+// optimisation; a stand-alone reduction built from these headers is exact
+// with this call out of line, or inlined at -O1, -O0 or with -G.)
+template <int n, typename R>
+__device__ __noinline__ void root_chol_inverse(const R* C, R* Cinv, LogDetAcc<R>& ld, bool& ok) {
+  chol_inverse<n, R>(C, Cinv, ld, ok);
+}
+
 // ------------------------------------------------------------ block reductions
 
 // Sum of NV values over the thread block (blockDim.x a multiple of 32); every
@@ -381,7 +390,7 @@ PGV_BIG TrialOut cr_trial(const PlanDesc& P, double beta_d, int cur, int out, do
     R* sp = scr;
     R D[np], Di[np];
     ld_packed<n, R>(sp + S::oDA, D);
-    chol_inverse<n, R>(D, Di, ldA, okA);
+    root_chol_inverse<n, R>(D, Di, ldA, okA);
     st_packed<n, R>(sp + S::oDA, Di);
     st_sym<n, R>(Sd_out, Di);
     if (wm) {

@@ -10,6 +10,7 @@
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
+#include <string.h>
 
 #include "pgvimp_plan.h"
 
@@ -171,12 +172,20 @@ struct LogDetAcc<df64> {
   df64 mant;
   int expo;
   PGV_HD void init() { mant = df_make(1.0f, 0.0f); expo = 0; }
+  // renormalises mant.hi into [0.5, 1): its exponent read from the float's
+  // bits, both parts scaled by the exact power of two 2^-e built the same way
+  // (integer and FP32 operations only; the pivot products stay well inside
+  // the float range)
   PGV_HD void mul(df64 v) {
     mant = mant * v;
-    int e;
-    frexpf(mant.hi, &e);
-    mant.hi = ldexpf(mant.hi, -e);
-    mant.lo = ldexpf(mant.lo, -e);
+    int bits;
+    memcpy(&bits, &mant.hi, sizeof(bits));
+    const int e = ((bits >> 23) & 0xff) - 126;
+    const int sbits = (127 - e) << 23;
+    float sc;
+    memcpy(&sc, &sbits, sizeof(sc));
+    mant.hi = PGV_FMUL(mant.hi, sc);
+    mant.lo = PGV_FMUL(mant.lo, sc);
     expo += e;
   }
   PGV_HD double log_value() const { return log(r_to(mant)) + expo * 0.69314718055994530942; }

@@ -5,17 +5,26 @@
 
 namespace pgv {
 
+// FP32 reciprocal estimate: the hardware approximation (at most 1 ulp off)
+// on the device, IEEE division on the host.
+PGV_HD float df_rcp_estimate(float a) {
 #ifdef __CUDA_ARCH__
-#define PGV_FRCP(a) __frcp_rn(a)
+  float r;
+  asm("rcp.approx.f32 %0, %1;" : "=f"(r) : "f"(a));
+  return r;
 #else
-#define PGV_FRCP(a) (1.0f / (a))
+  return 1.0f / a;
 #endif
+}
 
-// 1/v by one Newton-Raphson step from the correctly rounded FP32 reciprocal r
-// of v.hi: r (1 + e) with the residual e = 1 - v r formed by two FMAs.  As
-// |e| <= 2^-24, the step leaves a relative error of about e^2 + 2^-46.
+// 1/v by Newton-Raphson steps on the FP32 estimate r of 1/v.hi: one step in
+// FP32, r + r (1 - v.hi r), which brings r to within about 2^-24 of 1/v.hi;
+// then one double-float step r (1 + e) with the residual e = 1 - v r formed
+// by two FMAs, leaving a relative error of about e^2 + 2^-46.  FP32 and FMA
+// operations only.
 PGV_HD df64 df_rcp(df64 v) {
-  const float r = PGV_FRCP(v.hi);
+  float r = df_rcp_estimate(v.hi);
+  r = PGV_FFMA(r, PGV_FFMA(-v.hi, r, 1.0f), r);
   const float t = PGV_FFMA(-v.hi, r, 1.0f);
   const float e = PGV_FFMA(-v.lo, r, t);
   return df_fast_two_sum(r, PGV_FMUL(r, e));

@@ -396,24 +396,52 @@ PGV_BIG double prior_cost_of(const PlanDesc& P, int s) {
 
 // ------------------------------------------------------- quadrature (a2-a4)
 
+// The point robots' cost constants in the quadrature's arithmetic, converted
+// once per factor rather than at every sigma point (on B300 each FP64 -> FP32
+// conversion occupies the narrow FP64 pipe).
+template <typename QT>
+struct QuadConsts {
+  QT inv_cell, eps, w;   // 1/cell, hinge margin, weight of h^2
+};
+template <typename QT>
+PGV_DEV QuadConsts<QT> quad_consts(const PlanDesc& P) {
+  QuadConsts<QT> k;
+  k.inv_cell = (QT)P.inv_cell;
+  k.eps = (QT)P.eps;
+  k.w = (P.psi_form == 1) ? (QT)(1.0 / (P.sigma_obs * P.sigma_obs)) : (QT)P.sigma_obs;
+  return k;
+}
+
 // Collision cost at a state whose cost coordinates are mu_a + dx_a.  The grid
 // coordinate of the mean is pre-split into integer base + fraction (gb, gf).
 template <typename QT>
-PGV_DEV QT point_psi(const PlanDesc& P, const int* gb, const QT* gf, const QT* dx, const QT* mu_a) {
-  const QT ic = (QT)P.inv_cell;
-  if (P.cost_kind == PGVIMP_COST_POINT2D) {
-    QT s = sdf2<QT>(P.sdf, P.nx, P.ny, gb[0], gf[0] + dx[0] * ic, gb[1], gf[1] + dx[1] * ic);
-    return hinge_psi<QT>(P, (QT)P.eps - s);
-  }
-  if (P.cost_kind == PGVIMP_COST_POINT3D) {
-    QT s = sdf3<QT>(P.sdf, P.nx, P.ny, P.nz, gb[0], gf[0] + dx[0] * ic, gb[1], gf[1] + dx[1] * ic, gb[2],
-                    gf[2] + dx[2] * ic);
-    return hinge_psi<QT>(P, (QT)P.eps - s);
+PGV_DEV QT point_psi(const PlanDesc& P, const QuadConsts<QT>& k, const int* gb, const QT* gf, const QT* dx,
+                     const QT* mu_a) {
+  const QT ic = k.inv_cell;
+  if (P.cost_kind == PGVIMP_COST_POINT2D || P.cost_kind == PGVIMP_COST_POINT3D) {
+    QT s = (P.cost_kind == PGVIMP_COST_POINT2D)
+               ? sdf2<QT>(P.sdf, P.nx, P.ny, gb[0], gf[0] + dx[0] * ic, gb[1], gf[1] + dx[1] * ic)
+               : sdf3<QT>(P.sdf, P.nx, P.ny, P.nz, gb[0], gf[0] + dx[0] * ic, gb[1], gf[1] + dx[1] * ic, gb[2],
+                          gf[2] + dx[2] * ic);
+    QT h = k.eps - s;
+    h = h > (QT)0 ? h : (QT)0;
+    return k.w * h * h;
   }
   QT q[kMaxDof];
   for (int a = 0; a < P.arm_dof; ++a) q[a] = mu_a[a] + dx[a];
   return arm_cost<QT>(P, q);
 }
+
+// A recursion value in the quadrature's arithmetic (double-float to FP32 by
+// one FP32 add, no FP64 operation).
+template <typename QT>
+PGV_DEV QT r_toq(double v) { return (QT)v; }
+template <typename QT>
+PGV_DEV QT r_toq(df64 v);
+template <>
+PGV_DEV float r_toq<float>(df64 v) { return __fadd_rn(v.hi, v.lo); }
+template <>
+PGV_DEV double r_toq<double>(df64 v) { return r_to(v); }
 
 // Grid coordinate (mu - origin)/cell split into an exact integer part and a
 // fraction, evaluated in the recursion's arithmetic.
@@ -431,6 +459,13 @@ PGV_DEV void grid_split(df64 mu, double origin, double inv_cell, int& base, QT& 
   base = (int)fl;
   frac = (QT)((u.hi - fl) + u.lo);
 }
+
+// A moment (quadrature arithmetic) times the inverse temperature, in the
+// recursion's arithmetic: FP64 as a double product; double-float as the exact
+// float value times the double-float inverse temperature (no FP64 operation).
+PGV_DEV double scale_moment(float m, double it, double) { return (double)m * it; }
+PGV_DEV double scale_moment(double m, double it, double) { return m * it; }
+PGV_DEV df64 scale_moment(float m, double, df64 itr) { return df_make(m, 0.0f) * itr; }
 
 // E[psi_i] and the gradients g_i = Sigma^-1 E[(x-mu) psi],
 // G_i = -1/2 Sigma^-1 E[psi] + 1/2 Sigma^-1 E[(x-mu)(x-mu)^T psi] Sigma^-1
@@ -458,8 +493,9 @@ PGV_DEV bool quad_factor(const PlanDesc& P, int i, const R* mu_i, const R* S_ii,
   R L[nn], Li[nn];
   if (!chol_lead<n, R>(S_ii, dL, L, Li)) return false;
   QT Lq[nn], mua[kMaxN];
-  for (int e = 0; e < nn; ++e) Lq[e] = (QT)r_to(L[e]);
-  for (int a = 0; a < dc; ++a) mua[a] = (QT)r_to(mu_i[a]);
+  for (int e = 0; e < nn; ++e) Lq[e] = r_toq<QT>(L[e]);
+  for (int a = 0; a < dc; ++a) mua[a] = r_toq<QT>(mu_i[a]);
+  const QuadConsts<QT> kq = quad_consts<QT>(P);
   int gb[3] = {0, 0, 0};
   QT gf[3] = {0, 0, 0};
   if (P.cost_kind != PGVIMP_COST_ARM)
@@ -479,7 +515,7 @@ PGV_DEV bool quad_factor(const PlanDesc& P, int i, const R* mu_i, const R* S_ii,
         for (int c = 0; c <= a; ++c) s += Lq[a * n + c] * xi[c];
         dx[a] = s;
       }
-      const QT ps = point_psi<QT>(P, gb, gf, dx, mua);
+      const QT ps = point_psi<QT>(P, kq, gb, gf, dx, mua);
       const QT wp = (QT)row[dc] * ps;
       psi_c += (QT)row[dc + 1] * ps;          // level k-1: the trailing second moments
       M0 += wp;
@@ -493,6 +529,11 @@ PGV_DEV bool quad_factor(const PlanDesc& P, int i, const R* mu_i, const R* S_ii,
     const int p = P.gh_p;
     int Pn = 1;
     for (int a = 0; a < dc; ++a) Pn *= p;
+    QT xq[kMaxGH], wq[kMaxGH];   // the 1-D rule, converted once
+    for (int d = 0; d < p; ++d) {
+      xq[d] = (QT)P.gh_x[p * kMaxGH + d];
+      wq[d] = (QT)P.gh_w[p * kMaxGH + d];
+    }
     for (int l = 0; l < Pn; ++l) {
       QT xi[kMaxN];
       QT w = 1;
@@ -500,15 +541,15 @@ PGV_DEV bool quad_factor(const PlanDesc& P, int i, const R* mu_i, const R* S_ii,
       for (int a = dc - 1; a >= 0; --a) {
         int d = rem % p;
         rem /= p;
-        xi[a] = (QT)P.gh_x[p * kMaxGH + d];
-        w *= (QT)P.gh_w[p * kMaxGH + d];
+        xi[a] = xq[d];
+        w *= wq[d];
       }
       for (int a = 0; a < dc; ++a) {
         QT s = 0;
         for (int c = 0; c <= a; ++c) s += Lq[a * n + c] * xi[c];
         dx[a] = s;
       }
-      QT wp = w * point_psi<QT>(P, gb, gf, dx, mua);
+      QT wp = w * point_psi<QT>(P, kq, gb, gf, dx, mua);
       M0 += wp;
       for (int a = 0; a < dc; ++a) {
         QT t = wp * xi[a];
@@ -518,14 +559,14 @@ PGV_DEV bool quad_factor(const PlanDesc& P, int i, const R* mu_i, const R* S_ii,
     }
   } else {
     for (int a = 0; a < dc; ++a) dx[a] = 0;
-    psi_c = point_psi<QT>(P, gb, gf, dx, mua);
+    psi_c = point_psi<QT>(P, kq, gb, gf, dx, mua);
     M0 = (QT)(1.0 - dc / 3.0) * psi_c;
     const QT r3 = (QT)1.7320508075688772935, w6 = (QT)(1.0 / 6.0);
     for (int j = 0; j < dc; ++j) {
       for (int a = 0; a < dc; ++a) dx[a] = r3 * Lq[a * n + j];
-      QT pp = point_psi<QT>(P, gb, gf, dx, mua);
+      QT pp = point_psi<QT>(P, kq, gb, gf, dx, mua);
       for (int a = 0; a < dc; ++a) dx[a] = -r3 * Lq[a * n + j];
-      QT pm = point_psi<QT>(P, gb, gf, dx, mua);
+      QT pm = point_psi<QT>(P, kq, gb, gf, dx, mua);
       M0 += w6 * (pp + pm);
       M1[j] = w6 * r3 * (pp - pm);
       M2[j * dc + j] = (QT)0.5 * (pp + pm);
@@ -534,22 +575,23 @@ PGV_DEV bool quad_factor(const PlanDesc& P, int i, const R* mu_i, const R* S_ii,
   // gradient assembly: D = blockdiag(M2 - M0 I, (psi_c - M0) I [degree 3 only]);
   // the cost is divided by the temperature T-hat
   const double it = cur_inv_temp(P);
+  const R itr = r_from<R>(it);
   R D[nn];
   for (int e = 0; e < nn; ++e) D[e] = zero;
   const double m0 = (double)M0 * it;
-  const R m0r = r_from<R>(m0);
+  const R m0r = scale_moment(M0, it, itr);
   for (int a = 0; a < dc; ++a)
     for (int c = 0; c <= a; ++c) {
-      R v = r_from<R>((double)M2[a * dc + c] * it);
+      R v = scale_moment(M2[a * dc + c], it, itr);
       if (a == c) v = v - m0r;
       D[a * n + c] = v;
       D[c * n + a] = v;
     }
   if (deg3 || sparse)
-    for (int b = dc; b < n; ++b) D[b * n + b] = r_from<R>((double)psi_c * it) - m0r;
+    for (int b = dc; b < n; ++b) D[b * n + b] = scale_moment(psi_c, it, itr) - m0r;
   for (int r = 0; r < dL; ++r) {
     R s = zero;
-    for (int a = r; a < dc; ++a) s = r_fma(Li[a * n + r], r_from<R>((double)M1[a] * it), s);
+    for (int a = r; a < dc; ++a) s = r_fma(Li[a * n + r], scale_moment(M1[a], it, itr), s);
     g[r] = s;
   }
   R T[nn];
@@ -1150,6 +1192,11 @@ PGV_DEV bool slr_step(const PlanDesc& P, const double* xbar, const double* Sbar,
     const int p = P.gh_p;
     int Pn = 1;
     for (int a = 0; a < n; ++a) Pn *= p;
+    QT xq[kMaxGH], wq[kMaxGH];   // the 1-D rule, converted once
+    for (int d = 0; d < p; ++d) {
+      xq[d] = (QT)P.gh_x[p * kMaxGH + d];
+      wq[d] = (QT)P.gh_w[p * kMaxGH + d];
+    }
     for (int l = 0; l < Pn; ++l) {
       QT xi[n];
       QT w = 1;
@@ -1157,8 +1204,8 @@ PGV_DEV bool slr_step(const PlanDesc& P, const double* xbar, const double* Sbar,
       for (int a = n - 1; a >= 0; --a) {
         int d = rem % p;
         rem /= p;
-        xi[a] = (QT)P.gh_x[p * kMaxGH + d];
-        w *= (QT)P.gh_w[p * kMaxGH + d];
+        xi[a] = xq[d];
+        w *= wq[d];
       }
       accum(xi, w);
     }

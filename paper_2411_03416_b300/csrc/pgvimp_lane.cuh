@@ -82,6 +82,13 @@ PGV_DEV double halfsum_d(const Lane& x, double v) {
   return v + shx(x, v, 8);
 }
 
+// Cache hint: the line holding p, fetched into L1 ahead of its use (no
+// register is held for it).
+PGV_DEV void prefetch_l1(const void* p) { asm volatile("prefetch.L1 [%0];" ::"l"(p)); }
+// 2 v, exactly.
+PGV_DEV double twice(double v) { return v + v; }
+PGV_DEV df64 twice(df64 v) { return df_make(v.hi + v.hi, v.lo + v.lo); }
+
 // 1/v: IEEE division in FP64; for double-float one Newton-Raphson step from
 // the correctly rounded FP32 reciprocal r of v.hi, r (1 + e) with the
 // residual e = 1 - v r formed by two FMAs (|e| <= 2^-24, so the step leaves a
@@ -199,54 +206,48 @@ PGV_BIG TrialOut trial_lane(const Lane& x, const PlanDesc& P, double beta_d, int
   res.delta = 0.0;
   res.trace = 0.0;
   const bool ngd = (P.update == PGVIMP_UPDATE_NGD);
-  const R beta = r_from<R>(beta_d), beta2 = beta + beta, zero = r_fromf<R>(0.0f);
+  const R beta = r_from<R>(beta_d), zero = r_fromf<R>(0.0f);
   const R cL = ngd ? r_from<R>(1.0 - beta_d) : r_fromf<R>(1.0f);   // weight of Lambda_k
-  const R gM = ngd ? beta2 : zero;                                    // 2 beta G in M (NGD: M = A~)
 
-  // ---- forward: eliminate A~ and M, state by state; operands of state i+1
-  // are loaded while state i is eliminated
+  // ---- forward: eliminate A~ and M, state by state; the lines of state
+  // i+1's operands are fetched into L1 while state i is eliminated
   R SA = zero, SM = zero, vM = zero, q = zero;
   R mi_c = mu[c];
-  R K = Kd[l], G = GG[l], L = Ld[l], bg = bb[a] - gg[a];
-  R Eo = zero, EoT = zero, Lb = zero, mn_c = zero;
-  if (N > 0) {
-    Eo = Ko[l];
-    EoT = Ko[4 * c + a];
-    Lb = Lo[l];
-    mn_c = mu[kN + c];
-  }
   LogDetAcc<R> ldA;
   ldA.init();
   bool okA = true, okM = true;
   for (int i = 0; i <= N; ++i) {
-    // next state's operands
-    R K1 = zero, G1 = zero, L1 = zero, bg1 = zero, Eo1 = zero, EoT1 = zero, Lb1 = zero, mn1 = zero;
+    const size_t o = (size_t)i * kNN;
     if (i < N) {
-      const size_t o = (size_t)(i + 1) * kNN;
-      K1 = Kd[o + l];
-      G1 = GG[o + l];
-      L1 = Ld[o + l];
-      bg1 = bb[(size_t)(i + 1) * kN + a] - gg[(size_t)(i + 1) * kN + a];
+      const size_t o1 = o + kNN;
+      prefetch_l1(Kd + o1 + l);
+      prefetch_l1(GG + o1 + l);
+      prefetch_l1(Ld + o1 + l);
+      prefetch_l1(bb + (size_t)(i + 1) * kN + a);
+      prefetch_l1(gg + (size_t)(i + 1) * kN + a);
       if (i + 1 < N) {
-        Eo1 = Ko[o + l];
-        EoT1 = Ko[o + 4 * c + a];
-        Lb1 = Lo[o + l];
-        mn1 = mu[(size_t)(i + 2) * kN + c];
+        prefetch_l1(Ko + o1 + l);
+        prefetch_l1(Lo + o1 + l);
+        prefetch_l1(mu + (size_t)(i + 2) * kN + c);
       }
     }
+    const R K = Kd[o + l], G2 = twice(GG[o + l]), L = Ld[o + l];
     const R Lw = ngd ? cL * L : L;
     const R kb = beta * K;
-    R CA = r_fma(beta2, G, kb + Lw) - SA;
-    R CM = r_fma(gM, G, kb + Lw) - SM;
+    R CA = r_fma(beta, G2, kb + Lw) - SA;
+    R CM = (ngd ? r_fma(beta, G2, kb + Lw) : kb + Lw) - SM;
     R Kmu = rowsum(x, K * mi_c) + q;               // (K^-1 mu_k)_i, row-replicated
     R CiA = CA, CiM = CM;
     gj_inverse2(x, CiA, CiM, ldA, okA, okM);
-    R E = zero;
+    R E = zero, mn_c = zero;
     if (i < N) {
+      const R Eo = Ko[o + l], EoT = Ko[o + 4 * c + a], Lb = Lo[o + l];
+      mn_c = mu[(size_t)(i + 1) * kN + c];
       Kmu = Kmu + rowsum(x, EoT * mn_c);            // + K^-1_{i,i+1} mu_{i+1}
       q = rowsum(x, Eo * mi_c);                     // K^-1_{i+1,i} mu_i, for state i+1
       E = r_fma(beta, Eo, ngd ? cL * Lb : Lb);      // beta K^-1_{i+1,i} + c Lambda_{i+1,i}
     }
+    const R bg = bb[(size_t)i * kN + a] - gg[(size_t)i * kN + a];
     const R y = r_fma(beta, bg - Kmu, -vM);         // rhs of the reduced mean system
     const R y_c = sh(x, y, 4 * c + a);              // y_c in lane (a, c)
     const R z = rowsum(x, CiM * y_c);
@@ -263,7 +264,6 @@ PGV_BIG TrialOut trial_lane(const Lane& x, const PlanDesc& P, double beta_d, int
       sp[oWM + l] = WM;
     }
     mi_c = mn_c;
-    K = K1; G = G1; L = L1; bg = bg1; Eo = Eo1; EoT = EoT1; Lb = Lb1; mn_c = mn1;
   }
   __syncwarp(x.mask);
   if (!okA || !okM) return res;
@@ -289,34 +289,34 @@ PGV_BIG TrialOut trial_lane(const Lane& x, const PlanDesc& P, double beta_d, int
     const R mo = mu[(size_t)N * kN + a] + xn;
     dpn = mo - mubar[(size_t)N * kN + a];
     const R dpn_c = sh(x, dpn, 4 * c + a);
-    trc = r_fma(Lk - (Gk + Gk) - Kk, Sn, trc);
+    trc = r_fma(Lk - twice(Gk) - Kk, Sn, trc);
     dl = r_fma(xn * Lk, xn_c, dl);
     ktr = r_fma(Kk, Sn, ktr);
     kq = r_fma(dpn * Kk, dpn_c, kq);
     Sd_out[o + l] = s * Sn;
     if (c == 0) mo_out[(size_t)N * kN + a] = mo;
   }
-  // prefetch of state i's operands one step ahead
-  R Wn = zero, Cin = zero, WMTn = zero, zn = zero, Lkn = zero, Gkn = zero, Kkn = zero, Lon = zero, Kon = zero,
-    mun = zero, mbn = zero;
-  if (N > 0) {
-    const int i = N - 1;
-    const R* sp = scr + (size_t)i * kStride;
-    const size_t o = (size_t)i * kNN;
-    Wn = sp[oWA + l]; Cin = sp[oCi + l]; WMTn = sp[oWM + 4 * c + a]; zn = sp[oZ + a];
-    Lkn = Ld[o + l]; Gkn = GG[o + l]; Kkn = Kd[o + l]; Lon = Lo[o + l]; Kon = Ko[o + l];
-    mun = mu[(size_t)i * kN + a]; mbn = mubar[(size_t)i * kN + a];
-  }
   for (int i = N - 1; i >= 0; --i) {
-    const R W = Wn, Ci = Cin, WMT = WMTn, z = zn, Lk = Lkn, Gk = Gkn, Kk = Kkn, Lob = Lon, Kob = Kon, mui = mun,
-            mbi = mbn;
-    if (i > 0) {
-      const R* sp = scr + (size_t)(i - 1) * kStride;
-      const size_t o = (size_t)(i - 1) * kNN;
-      Wn = sp[oWA + l]; Cin = sp[oCi + l]; WMTn = sp[oWM + 4 * c + a]; zn = sp[oZ + a];
-      Lkn = Ld[o + l]; Gkn = GG[o + l]; Kkn = Kd[o + l]; Lon = Lo[o + l]; Kon = Ko[o + l];
-      mun = mu[(size_t)(i - 1) * kN + a]; mbn = mubar[(size_t)(i - 1) * kN + a];
+    if (i > 0) {   // the lines of state i-1's operands, fetched into L1 ahead of use
+      const R* sp1 = scr + (size_t)(i - 1) * kStride;
+      const size_t o1 = (size_t)(i - 1) * kNN;
+      prefetch_l1(sp1 + oWA + l);
+      prefetch_l1(sp1 + oCi + l);
+      prefetch_l1(sp1 + oWM + l);
+      prefetch_l1(sp1 + oZ + a);
+      prefetch_l1(Ld + o1 + l);
+      prefetch_l1(GG + o1 + l);
+      prefetch_l1(Kd + o1 + l);
+      prefetch_l1(Lo + o1 + l);
+      prefetch_l1(Ko + o1 + l);
+      prefetch_l1(mu + (size_t)(i - 1) * kN + a);
+      prefetch_l1(mubar + (size_t)(i - 1) * kN + a);
     }
+    const R* sp = scr + (size_t)i * kStride;
+    const size_t oi = (size_t)i * kNN;
+    const R W = sp[oWA + l], Ci = sp[oCi + l], WMT = sp[oWM + 4 * c + a], z = sp[oZ + a];
+    const R Lk = Ld[oi + l], Gk = GG[oi + l], Kk = Kd[oi + l], Lob = Lo[oi + l], Kob = Ko[oi + l];
+    const R mui = mu[(size_t)i * kN + a], mbi = mubar[(size_t)i * kN + a];
     const R T = mm(x, Sn, W);                      // Sigma~_{i+1} W_i = -Sigma~_{i+1,i}
     const R Si = Ci + mm_tn(x, W, T);              // C_i^-1 + W_i^T Sigma~_{i+1} W_i
     const R xn_c = sh(x, xn, 4 * c + a);
@@ -325,14 +325,15 @@ PGV_BIG TrialOut trial_lane(const Lane& x, const PlanDesc& P, double beta_d, int
     const R dpi = mo - mbi;
     const R xi_c = sh(x, xi, 4 * c + a);
     const R dpi_c = sh(x, dpi, 4 * c + a);
-    trc = r_fma(Lk - (Gk + Gk) - Kk, Si, trc);
-    trc = r_fma(Kob + Kob - (Lob + Lob), T, trc);
+    const R Ko2 = twice(Kob);
+    trc = r_fma(Lk - twice(Gk) - Kk, Si, trc);
+    trc = r_fma(Ko2 - twice(Lob), T, trc);
     dl = r_fma(xi * Lk, xi_c, dl);
-    dl = r_fma((xn + xn) * Lob, xi_c, dl);
+    dl = r_fma(twice(xn) * Lob, xi_c, dl);
     ktr = r_fma(Kk, Si, ktr);
-    ktr = r_fma(-(Kob + Kob), T, ktr);
+    ktr = r_fma(-Ko2, T, ktr);
     kq = r_fma(dpi * Kk, dpi_c, kq);
-    kq = r_fma((dpn + dpn) * Kob, dpi_c, kq);
+    kq = r_fma(twice(dpn) * Kob, dpi_c, kq);
     const size_t o = (size_t)i * kNN;
     Sd_out[o + l] = s * Si;
     So_out[o + l] = ms * T;
