@@ -102,21 +102,35 @@ def fp32_peak_tflops():
     return 148 * 128 * 2 * 2.032e9 / 1e12
 
 
-# FP32 flops per emulated FP64 flop in the double-float recursions, from the
-# implementation: a double-float FMA is 4 FFMA/FMUL + 11 FADD/FSUB (18 flops
-# for 2 FP64 flops), a multiply 10 flops, an add 11 flops; with the trial's
-# measured FP64 op mix (600 FMA : 129 add : 168 mul per state) that is
-# (600*18 + 129*11 + 168*10) / (600*2 + 129 + 168) = 9.29.
+# FP32 flops per emulated FP64 flop in the double-float recursions, counted
+# from the double-float primitives: an FMA is 4 FFMA/FMUL + 11 FADD/FSUB (18
+# flops for 2 FP64 flops), a multiply 10 flops, an add 11 flops; with the
+# trial's FP64 op mix (600 FMA : 129 add : 168 mul per state) that is
+# (600*18 + 129*11 + 168*10) / (600*2 + 129 + 168) = 9.29.  This is the
+# algorithmic FP32 work per FP64 flop, what `achieved` counts.
 DF_EXPANSION = 9.29
 
-# DRAM bytes (read + write) per state per trial of the double-float fused
-# kernel (k_iterate<4, float, df64>, 128 registers), from one ncu capture of a
-# 2,368-plan, 2-iteration dense-horizon launch: 59.25 GB read + 23.60 GB
-# written over 52,096 trials x 751 states.  The algorithmic touch of one
-# state-trial (both sweeps re-read the five blocks, the scratch is written
-# and read back, the outputs written) is about 2.5 KB, so the kernel makes no
-# wasted re-reads.  A full launch's traffic is this times its state-trials.
-DF_DRAM_BYTES_PER_STATE_TRIAL = 82.85e9 / (52096 * 751)
+# What the lane-form kernel (k_iterate_lane, sixteen lanes per plan) executes,
+# from ncu counters of 2,368 dense-horizon plans x 30 iterations (N = 750):
+# with double-float recursions 5.244e12 FP32 flops (2 FFMA + FADD + FMUL) over
+# 336,790 trials x 751 states = 20,720 per state-trial; with FP64 recursions
+# 196 FP32 flops per state-trial (the quadrature) and 3,424 FP64 flops per
+# state-trial against the 1,685 counted (its per-lane pivot reciprocals are
+# IEEE divisions and its row sums are replicated over the row's four lanes).
+# The double-float recursions thus execute 20,524 FP32 flops per state-trial,
+# a measured expansion of 12.2 FP32 flops per counted FP64 flop.
+LANE_DF_EXECUTED_FP32_PER_STATE_TRIAL = 5.244e12 / (336790 * 751)
+LANE_DF_MEASURED_EXPANSION = 12.2
+
+# DRAM bytes (read + write) per state per trial of the lane-form double-float
+# kernel, from the same capture: 416.2 GB read + 178.6 GB written over 336,790
+# trials x 751 states = 2,352 B.  The algorithmic touch of one state-trial (both
+# sweeps read the five blocks, the scratch is written and read back, the
+# outputs written) is about 2.5 KB, so the kernel makes no wasted re-reads.  A
+# full launch's traffic is this times its state-trials (traffic grows in
+# proportion to the state-trials: the per-plan working set, ~1 MB, exceeds
+# what L2 holds for a resident wave of plans).
+LANE_DF_DRAM_BYTES_PER_STATE_TRIAL = (416.199e9 + 178.616e9) / (336790 * 751)
 
 
 # --------------------------------------------------------------------- clocks
@@ -516,7 +530,7 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--batch", type=int, default=75776,
-                    help="plans per GPU (one thread each; 75,776 = 16 warps per SM, one wave)")
+                    help="plans per GPU (75,776: sixteen lanes each in the lane form, eight waves of 1,024 threads per SM)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--plain-steps", type=int, default=1)
@@ -605,7 +619,7 @@ def main():
     value = args.batch * ws * args.steps / t_max
 
     # ---- dominant kernel: the fused-iteration launch, timed inside the timed steps.  Each run's
-    # interval also holds its prior, init and finalize launches, 0.7% of it by the ncu launch list,
+    # interval also holds its prior, init and finalize launches, 1.9% of it by the ncu launch list,
     # so the achieved rate below is a slight underestimate.  Trial counts come from the last step.
     run_ms = [a.elapsed_time(b[1]) for a, b in zip(ev_run, ev)]
     bm.download_results(sh)
@@ -618,22 +632,32 @@ def main():
     state_trials = sum((pb.N + 1) * t for pb, t in zip(probs, trials))
     flops = algorithmic_fp64_flops(probs, trials)
     k_ms = sum(run_ms) / len(run_ms)
-    traffic, traffic_note = None, "no capture of this form's kernel"
+    traffic, traffic_note, executed = None, "no capture of this form's kernel", None
+    lane = head == 2   # the default form of n = 4 plans: the lane form with double-float, the thread form otherwise
     if head == 2:
-        traffic = DF_DRAM_BYTES_PER_STATE_TRIAL * state_trials
-        traffic_note = ("bytes per launch: ncu dram bytes per state-trial of a 2,368-plan capture x this launch's "
-                        f"{state_trials} state-trials ({traffic / (k_ms / 1000.0) / 1e9:.0f} GB/s over the launch)")
         flops32 = flops * DF_EXPANSION
         achieved = flops32 / (k_ms / 1000.0) / 1e12
         peak = fp32_peak_tflops()
-        roof_kind = ("FP32 pipe (double-float recursions): FP64-equivalent flops x 9.29 FP32 flops each; peak derived "
-                     "from unit counts and clock (measured FFMA loop: 68.2)")
-        kernel_name = "k_iterate<4, float, df64> (fused proximal iterations)"
+        roof_kind = ("FP32 pipe (double-float recursions): counted FP64 flops x 9.29 FP32 flops each (the double-float "
+                     "primitives' op counts); peak derived from unit counts and clock (measured FFMA loop: 68.2)")
+        if lane:
+            traffic = LANE_DF_DRAM_BYTES_PER_STATE_TRIAL * state_trials
+            traffic_note = ("bytes per launch: ncu dram bytes per state-trial of a 2,368-plan, 30-iteration capture of "
+                            f"this kernel x this launch's {state_trials} state-trials "
+                            f"({traffic / (k_ms / 1000.0) / 1e9:.0f} GB/s over the launch)")
+            ex = LANE_DF_EXECUTED_FP32_PER_STATE_TRIAL * state_trials / (k_ms / 1000.0) / 1e12
+            executed = {"fp32_tflops": ex, "frac": ex / peak, "measured_df_expansion": LANE_DF_MEASURED_EXPANSION,
+                        "note": ("FP32 flops the kernel executes (ncu counters per state-trial x state-trials), "
+                                 "replicated lane work included")}
+            kernel_name = "k_iterate_lane<float, df64> (fused iterations, lane form: 16 lanes per plan)"
+        else:
+            kernel_name = "k_iterate<4, float, df64> (fused iterations, thread form)"
     else:
         achieved = flops / (k_ms / 1000.0) / 1e12
         peak = fp64_peak_tflops()
         roof_kind = "FP64 derived from unit counts and clock (measured DFMA loop: 0.935)"
-        kernel_name = f"k_iterate<4, {'float' if head == 1 else 'double'}, double> (fused proximal iterations)"
+        kernel_name = (f"k_iterate_lane<{'float' if head == 1 else 'double'}, double> (lane form)" if lane else
+                       f"k_iterate<4, {'float' if head == 1 else 'double'}, double> (fused iterations, thread form)")
 
     # ---- e2e through the C ABI with host buffers
     h2d, d2h_full, d2h = bm.io_bytes()
@@ -679,11 +703,11 @@ def main():
                      "fp64_equivalent": {"achieved": flops / (k_ms / 1000.0) / 1e12, "peak": fp64_peak_tflops(),
                                          "frac": flops / (k_ms / 1000.0) / 1e12 / fp64_peak_tflops(),
                                          "note": "the method's FP64 flops against the FP64 pipe's peak"},
-                     "traffic": traffic, "traffic_note": traffic_note,
+                     "traffic": traffic, "traffic_note": traffic_note, "executed": executed,
                      "kernel": kernel_name, "kernel_ms": k_ms, "peak_kind": roof_kind,
                      "kernel_timing": ("CUDA events on the launching stream around the batch run of every timed "
                                        "step, averaged; the interval adds the prior, init and finalize launches "
-                                       "(0.7% of it)"),
+                                       "(1.9% of it)"),
                      "algorithmic_fp64_equivalent_flops": flops},
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": "plans/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,

@@ -21,7 +21,8 @@ SOURCES = ["pgvimp_api.cu", "pgvimp_noalloc.cu", "pgvimp_server.cu", "k4_lane_df
            "k4_lane_f64.cu"] + [f"k{n}_{part}.cu" for n in (14, 6, 4)
                                for part in ("iter_df", "iter_f32", "cta_f32", "iter_f64", "cta_f64",
                                             "cta_df", "aux", "aux_df", "rows")]
-HEADERS = ["pgvimp_device.cuh", "pgvimp_dfx.cuh", "pgvimp_kernels.cuh", "pgvimp_cr.cuh", "pgvimp_lane.cuh", "pgvimp_plan.h",
+HEADERS = ["pgvimp_device.cuh", "pgvimp_dfx.cuh", "pgvimp_kernels.cuh", "pgvimp_cr.cuh", "pgvimp_crw.cuh",
+           "pgvimp_lane.cuh", "pgvimp_plan.h",
            "pgvimp_launch.h", "pgvimp_internal.h", "pgvimp_pool.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 EXTRA_FLAGS = {}   # per-unit extra nvcc flags
@@ -41,7 +42,7 @@ def _headers_of(src: str):
     if src.startswith("k"):
         base += ["pgvimp_device.cuh", "pgvimp_kernels.cuh", "pgvimp_launch.h"]
         if "_cta_" in src:
-            base += ["pgvimp_cr.cuh"]
+            base += ["pgvimp_cr.cuh", "pgvimp_crw.cuh", "pgvimp_dfx.cuh"]
         if "_lane_" in src:
             base += ["pgvimp_lane.cuh", "pgvimp_dfx.cuh"]
     elif src == "pgvimp_api.cu":

@@ -26,7 +26,7 @@ namespace pgv {
 // the lane form of the fused iterations (n = 4, sixteen lanes per plan).
 static cudaError_t launch_phase(int n, const Launch& L, int phase, int arg_i, double arg_d, int precision, int tpb,
                                 bool lane) {
-  constexpr int PRIOR = 100, INIT = 101, ITER = 102, SLR = 103;
+  constexpr int PRIOR = 100, INIT = 101, ITER = 102, SLR = 103, RELIN = 104, FIN = 106, WORKING = 107;
   const bool rows = (phase == PGVIMP_PHASE_MARGINALS || phase == PGVIMP_PHASE_QUAD || phase == PGVIMP_PHASE_TRIAL);
   const bool df = (precision == PGVIMP_PREC_MIXED_DF);
   const int qt32 = (precision != PGVIMP_PREC_PLAIN_FP64);
@@ -43,7 +43,8 @@ static cudaError_t launch_phase(int n, const Launch& L, int phase, int arg_i, do
         return qt32 ? launch_iter_cta<N_, float, double>(L, arg_i, tpb)                                   \
                     : launch_iter_cta<N_, double, double>(L, arg_i, tpb);                                 \
       }                                                                                                   \
-      if (phase == INIT || phase == SLR || (phase == PRIOR && arg_i == 1))                                \
+      if (phase == INIT || phase == SLR || phase == PRIOR || phase == RELIN || phase == FIN ||            \
+          phase == WORKING)                                                                               \
         return df ? launch_aux_cta<N_, df64>(L, phase, arg_i, qt32, tpb)                                  \
                   : launch_aux_cta<N_, double>(L, phase, arg_i, qt32, tpb);                               \
     }                                                                                                     \
@@ -521,9 +522,11 @@ void plan_layout(BatchImpl& B) {
     L.altv = take(work, 8 * (slr ? N * n : 1));
     L.xbar = take(work, 8 * (slr ? (N + 1) * n : 1));
     // per-state scratch: the sequential sweeps need 3n^2 + n, the cyclic
-    // reduction of the block form 2 npe + 6 n^2 + 2 n (npe: packed, even)
+    // reduction of the block form 2 npe + 6 n^2 + 2 n (npe: packed, even),
+    // its warp-cooperative form 8 n^2 + 2 n
     const size_t np = n * (n + 1) / 2, npe = np + (np & 1);
-    const size_t scr_state = B.tpb ? std::max(3 * nn + n, 2 * npe + 6 * nn + 2 * n) : 3 * nn + n;
+    const size_t scr_state =
+        B.tpb ? std::max(std::max(3 * nn + n, 2 * npe + 6 * nn + 2 * n), 8 * nn + 2 * n) : 3 * nn + n;
     L.scr = take(work, 8 * (N + 1) * scr_state);
   }
   B.in_bytes = align256(in);

@@ -23,9 +23,16 @@
 // cross blocks live in slot min(l, r) of the So buffer, so that after level 1
 // slot j holds Sigma_{j+1,j}.
 #pragma once
+#include "pgvimp_crw.cuh"
 #include "pgvimp_kernels.cuh"
 
 namespace pgv {
+
+// The warp-cooperative form of the trial (pgvimp_crw.cuh) serves n >= 6, whose
+// blocks do not fit one thread's registers; n = 4 keeps one thread per
+// elimination.
+template <int n>
+constexpr bool kCrWarp = (n >= 6);
 
 // Per-state scratch of the cyclic reduction (R elements, 16-byte aligned
 // sub-blocks): working diagonal blocks of both systems (their inverses after
@@ -140,30 +147,6 @@ PGV_DEV void sub_mv(const R* X, const R* v, R* y, bool trans) {
 template <int n, typename R>
 __device__ __noinline__ void root_chol_inverse(const R* C, R* Cinv, LogDetAcc<R>& ld, bool& ok) {
   chol_inverse<n, R>(C, Cinv, ld, ok);
-}
-
-// ------------------------------------------------------------ block reductions
-
-// Sum of NV values over the thread block (blockDim.x a multiple of 32); every
-// thread receives the same totals (same summation order in every thread).
-template <int NV>
-__device__ __forceinline__ void block_sum(double (&v)[NV], double* red) {
-#pragma unroll
-  for (int k = 0; k < NV; ++k)
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  __syncthreads();
-  if (lane == 0)
-#pragma unroll
-    for (int k = 0; k < NV; ++k) red[w * NV + k] = v[k];
-  __syncthreads();
-#pragma unroll
-  for (int k = 0; k < NV; ++k) {
-    double s = 0.0;
-    for (int j = 0; j < nw; ++j) s += red[j * NV + k];
-    v[k] = s;
-  }
 }
 
 // ------------------------------------------------------------ trial (a5), cyclic reduction
@@ -601,7 +584,7 @@ PGV_BIG void cr_accept_precision(const PlanDesc& P, double beta_d) {
 // with the quadrature spread over the block's threads and cyclic-reduction
 // trials.
 template <int n, typename QT, typename R>
-PGV_BIG void cr_iterate_once(const PlanDesc& P, double* red) {
+PGV_BIG void cr_iterate_once(const PlanDesc& P, double* red, R* wsm) {
   constexpr int nn = n * n;
   double* sc = P.scal;
   if (temp_switch_due(P)) {            // uniform: every thread reads the same slots
@@ -656,7 +639,9 @@ PGV_BIG void cr_iterate_once(const PlanDesc& P, double* red) {
   int into = oa, halvings = 0;
   bool searching = false;
   for (;;) {
-    TrialOut Rt = cr_trial<n, R>(P, beta, cur, into, logdet_k, false, red);
+    TrialOut Rt;
+    if constexpr (kCrWarp<n>) Rt = crw::trial<n, R>(P, beta, cur, into, logdet_k, false, red, wsm);
+    else Rt = cr_trial<n, R>(P, beta, cur, into, logdet_k, false, red);
     ++trials;
     if (Rt.pd && has_eps) margin = fmin(margin, fabs(Rt.kl - eps) / eps);
     const bool feas = Rt.pd && (Rt.kl <= eps);
@@ -677,7 +662,10 @@ PGV_BIG void cr_iterate_once(const PlanDesc& P, double* red) {
     beta = 0.5 * (lo + hi);
     into = (best == oa) ? ob : oa;
   }
-  if (best >= 0) cr_accept_precision<n, R>(P, best_beta);
+  if (best >= 0) {
+    if constexpr (kCrWarp<n>) crw::accept_precision<n, R>(P, best_beta);
+    else cr_accept_precision<n, R>(P, best_beta);
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
     if (k < P.log_cap) {
@@ -706,7 +694,7 @@ PGV_BIG void cr_iterate_once(const PlanDesc& P, double* red) {
 
 // Initial iterate (as init_plan) with its marginals by cyclic reduction.
 template <int n, typename R>
-PGV_BIG void cr_init_plan(const PlanDesc& P, double* red) {
+PGV_BIG void cr_init_plan(const PlanDesc& P, double* red, R* wsm) {
   constexpr int nn = n * n;
   double* sc = P.scal;
   const int N = P.N, nq = P.nq;
@@ -738,7 +726,9 @@ PGV_BIG void cr_init_plan(const PlanDesc& P, double* red) {
     }
   }
   __syncthreads();
-  TrialOut M = cr_trial<n, R>(P, 0.0, 0, 0, 0.0, true, red);
+  TrialOut M;
+  if constexpr (kCrWarp<n>) M = crw::trial<n, R>(P, 0.0, 0, 0, 0.0, true, red, wsm);
+  else M = cr_trial<n, R>(P, 0.0, 0, 0, 0.0, true, red);
   __syncthreads();
   if (threadIdx.x == 0) {
     if (!M.pd) {
@@ -758,26 +748,35 @@ PGV_BIG void cr_init_plan(const PlanDesc& P, double* red) {
 
 // ------------------------------------------------------------ kernels (one block per plan)
 
+// Dynamic shared memory of a block-form launch: the per-warp staging of the
+// warp-cooperative trial, none otherwise.
+template <int n, typename R>
+constexpr size_t cr_dyn_smem(int tpb) {
+  return kCrWarp<n> ? (size_t)(tpb / 32) * crw::Lay<n>::ws * sizeof(R) : 0;
+}
+
 template <int n, typename QT, typename R>
 __global__ void __launch_bounds__(kCrMaxThreads) k_iterate_cta(const PlanDesc* __restrict__ descs, int count,
                                                                int iters) {
   __shared__ double red[(kCrMaxThreads / 32) * 4];
+  extern __shared__ __align__(16) unsigned char cr_dyn[];
   if ((int)blockIdx.x >= count) return;
   const PlanDesc& P = descs[blockIdx.x];
   for (int it = 0; it < iters; ++it) {
     if (P.scal[S_STATUS] != 0.0 || P.scal[S_INIT] == 0.0) return;
     if ((int)P.scal[S_KIN] >= P.iters) return;
-    cr_iterate_once<n, QT, R>(P, red);
+    cr_iterate_once<n, QT, R>(P, red, reinterpret_cast<R*>(cr_dyn));
   }
 }
 
 template <int n, typename R>
 __global__ void __launch_bounds__(kCrMaxThreads) k_init_cta(const PlanDesc* __restrict__ descs, int count) {
   __shared__ double red[(kCrMaxThreads / 32) * 4];
+  extern __shared__ __align__(16) unsigned char cr_dyn[];
   if ((int)blockIdx.x >= count) return;
   const PlanDesc& P = descs[blockIdx.x];
   if (P.scal[S_STATUS] != 0.0) return;
-  cr_init_plan<n, R>(P, red);
+  cr_init_plan<n, R>(P, red, reinterpret_cast<R*>(cr_dyn));
 }
 
 // ------------------------------------------------------------ SLR and the LTV prior (a6, a0), block form
@@ -824,38 +823,56 @@ __global__ void __launch_bounds__(kCrMaxThreads) k_slr_cta(const PlanDesc* __res
   if (!ok && threadIdx.x == 0) P.scal[S_STATUS] = 4.0;
 }
 
-// Prior of the SLR linearisation (LTV, Alg. 2): the per-step Van Loan
-// factors in parallel, the block assembly of K^-1 and b in parallel (the
-// same expressions as prior_build), then the block solve for mu_bar on one
-// thread.  Per-step scratch: Phi_i, Q_i^-1, u_i.
+// The GP prior (Sec. 3, Alg. 1 line 1; for mode 1 the SLR linearisation's
+// LTV prior of Alg. 2) with its work spread over the block.  First the Van
+// Loan factors Phi_i, Q_i, u_i, one thread per step (a single step for a
+// time-invariant system), stored to the per-step scratch with scalar stores.
+// Then one warp per state assembles, in shared memory with the warp
+// routines of pgvimp_crw.cuh (FP64),
+//   K^-1_ii = C_i + Phi_i^T Q_i^-1 Phi_i,   b_i = c_i - Phi_i^T Q_i^-1 u_i,
+//   K^-1_{i+1,i} = -Q_i^-1 Phi_i,
+// with the carries C_0 = K_0^-1, c_0 = K_0^-1 mu_0, C_i = Q_{i-1}^-1,
+// c_i = Q_{i-1}^-1 u_{i-1}, and at i = N the terminal K_N^-1, K_N^-1 mu_N in
+// place of the step terms (the expressions of prior_build), all scaled by the
+// current inverse temperature.  mu_bar follows in k_prior_solve_cta.  (Built
+// with thread-local n x n arrays on sm_103a, this assembly returned wrong
+// blocks for some horizons and block widths; the warp form holds no block in
+// thread-local memory.)
 template <int n, typename R>
-__global__ void __launch_bounds__(kCrMaxThreads) k_prior_ltv_cta(const PlanDesc* __restrict__ descs, int count) {
+__global__ void __launch_bounds__(kCrMaxThreads) k_prior_cta(const PlanDesc* __restrict__ descs, int count,
+                                                             int mode) {
   constexpr int nn = n * n, SS = 2 * nn + n;
+  using Ly = crw::Lay<n>;
+  static_assert(sizeof(R) == sizeof(double), "the warp staging is sized in 8-byte elements");
+  extern __shared__ __align__(16) unsigned char cr_dyn[];
   if ((int)blockIdx.x >= count) return;
   const PlanDesc& P = descs[blockIdx.x];
   if (P.scal[S_STATUS] != 0.0) return;
+  const bool use_ltv = (mode == 1);
+  const bool lti = !use_ltv && !P.A_per_step && !P.a_per_step;
   const int N = P.N, m = P.m;
   double* scr = P.scr;
   bool ok = true;
   {
-    double Wn[nn];
-    for (int r = 0; r < n; ++r)
-      for (int c = 0; c < n; ++c) {
-        double s = 0.0;
-        for (int k = 0; k < m; ++k)
-          for (int l = 0; l < m; ++l) s += P.B[r * m + k] * P.Qc[k * m + l] * P.B[c * m + l];
-        Wn[r * n + c] = s;
-      }
-    for (int i = threadIdx.x; i < N; i += blockDim.x) {
-      double A[nn], av[n], Phi[nn], Q[nn], Qi[nn], u[n];
-      for (int e = 0; e < nn; ++e) A[e] = P.Altv[(size_t)i * nn + e];
-      for (int a = 0; a < n; ++a) av[a] = P.altv[(size_t)i * n + a];
+    const int steps = lti ? 1 : N;
+    for (int i = threadIdx.x; i < steps; i += blockDim.x) {
+      double Wn[nn], A[nn], av[n], Phi[nn], Q[nn], u[n];
+      for (int r = 0; r < n; ++r)
+        for (int c = 0; c < n; ++c) {
+          double s = 0.0;
+          for (int k = 0; k < m; ++k)
+            for (int l = 0; l < m; ++l) s += P.B[r * m + k] * P.Qc[k * m + l] * P.B[c * m + l];
+          Wn[r * n + c] = s;
+        }
+      const double* Ai = use_ltv ? P.Altv + (size_t)i * nn : (P.A_per_step ? P.A + (size_t)i * nn : P.A);
+      for (int e = 0; e < nn; ++e) A[e] = Ai[e];
+      for (int a = 0; a < n; ++a)
+        av[a] = use_ltv ? P.altv[(size_t)i * n + a] : (P.a ? (P.a_per_step ? P.a[(size_t)i * n + a] : P.a[a]) : 0.0);
       ok = van_loan<n>(A, av, Wn, P.dt, Phi, Q, u) && ok;
-      ok = spd_inverse_full<n>(Q, Qi) && ok;
-      double* sp = scr + (size_t)i * SS;
+      volatile double* sp = scr + (size_t)i * SS;
       for (int e = 0; e < nn; ++e) {
         sp[e] = Phi[e];
-        sp[nn + e] = Qi[e];
+        sp[nn + e] = Q[e];
       }
       for (int a = 0; a < n; ++a) sp[2 * nn + a] = u[a];
     }
@@ -865,78 +882,184 @@ __global__ void __launch_bounds__(kCrMaxThreads) k_prior_ltv_cta(const PlanDesc*
   R* Kd = rp<R>(P.Kd);
   R* Ko = rp<R>(P.Ko);
   R* b = rp<R>(P.b);
-  for (int i = threadIdx.x; i <= N; i += blockDim.x) {
-    double carry_d[nn], carry_b[n], blk[nn], bv[n];
-    if (i == 0) {
-      ok = spd_inverse_full<n>(P.K0, carry_d) && ok;
-      for (int a = 0; a < n; ++a) {
-        double s = 0.0;
-        for (int c = 0; c < n; ++c) s = fma(carry_d[a * n + c], P.mu0[c], s);
-        carry_b[a] = s;
-      }
-    } else {
-      const double* sp = scr + (size_t)(i - 1) * SS;   // Q_{i-1}^-1 and Q_{i-1}^-1 u_{i-1}
-      for (int e = 0; e < nn; ++e) carry_d[e] = sp[nn + e];
-      for (int a = 0; a < n; ++a) {
-        double s = 0.0;
-        for (int c = 0; c < n; ++c) s = fma(sp[nn + a * n + c], sp[2 * nn + c], s);
-        carry_b[a] = s;
-      }
-    }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, NW = blockDim.x >> 5;
+  double* ws = reinterpret_cast<double*>(cr_dyn) + (size_t)warp * Ly::ws;
+  double* S0 = ws;            // carry C_i
+  double* S1 = ws + nn;       // Phi_i, or K_N^-1
+  double* S2 = ws + 2 * nn;   // Q_i^-1
+  double* S3 = ws + 3 * nn;   // Phi_i^T Q_i^-1
+  double* S4 = ws + 4 * nn;   // C_i + Phi^T Q^-1 Phi
+  double* S5 = ws + 5 * nn;   // -Q_i^-1 Phi_i
+  double* row = ws + Ly::oRow;
+  double* col = ws + Ly::oCol;
+  double* V0 = ws + Ly::oV;   // carry c_i
+  double* V1 = V0 + n;        // u_{i-1}, mu_0; then u_i or mu_N
+  double* V2 = V1 + n;        // b_i before scaling
+  LogDetAcc<double> ldd;
+  ldd.init();
+  for (int i = warp; i <= N; i += NW) {
+    // carry: K_0^-1 (c = K_0^-1 mu_0), or Q_{i-1}^-1 (c = Q_{i-1}^-1 u_{i-1})
+    const double* spp = scr + (size_t)(lti ? 0 : (i > 0 ? i - 1 : 0)) * SS;
+#pragma unroll 1
+    for (int e = lane; e < nn; e += 32) S0[e] = (i == 0) ? P.K0[e] : spp[nn + e];
+    if (lane < n) V1[lane] = (i == 0) ? P.mu0[lane] : spp[2 * nn + lane];
+    crw::winv<n, double>(lane, S0, row, col, ldd, ok);
+    crw::mv<n, double>(lane, S0, false, V1, nullptr, V0, false);
+    __syncwarp();
     if (i < N) {
-      const double* sp = scr + (size_t)i * SS;
-      const double *Phi = sp, *Qi = sp + nn, *u = sp + 2 * nn;
-      double PtQi[nn], T1[nn];
-      for (int r = 0; r < n; ++r)
-        for (int c = 0; c < n; ++c) {
-          double s = 0.0;
-          for (int k = 0; k < n; ++k) s = fma(Phi[k * n + r], Qi[k * n + c], s);
-          PtQi[r * n + c] = s;
-        }
-      for (int r = 0; r < n; ++r)
-        for (int c = 0; c < n; ++c) {
-          double s = 0.0;
-          for (int k = 0; k < n; ++k) s = fma(PtQi[r * n + k], Phi[k * n + c], s);
-          T1[r * n + c] = s;
-        }
-      for (int e = 0; e < nn; ++e) blk[e] = (carry_d[e] + T1[e]) * it;
-      for (int a = 0; a < n; ++a) {
-        double s = carry_b[a];
-        for (int c = 0; c < n; ++c) s = fma(-PtQi[a * n + c], u[c], s);
-        bv[a] = s * it;
+      const double* sp = scr + (size_t)(lti ? 0 : i) * SS;
+#pragma unroll 1
+      for (int e = lane; e < nn; e += 32) {
+        S1[e] = sp[e];
+        S2[e] = sp[nn + e];
       }
-      double Eo[nn];
-      for (int r = 0; r < n; ++r)
-        for (int c = 0; c < n; ++c) {
-          double s = 0.0;
-          for (int k = 0; k < n; ++k) s = fma(Qi[r * n + k], Phi[k * n + c], s);
-          Eo[r * n + c] = -s * it;
-        }
-      st_blk_from_double<n, R>(Ko + (size_t)i * nn, Eo);
+      if (lane < n) V1[lane] = sp[2 * nn + lane];
+      crw::winv<n, double>(lane, S2, row, col, ldd, ok);
+      crw::mm<n, double>(lane, S1, S2, nullptr, S3, 1, 0, 0);     // Phi^T Q^-1
+      crw::mm<n, double>(lane, S2, S1, nullptr, S5, 0, 0, 1);     // -Q^-1 Phi
+      __syncwarp();
+      crw::mm<n, double>(lane, S3, S1, S0, S4, 0, 0, 0);          // C + Phi^T Q^-1 Phi
+      crw::mv<n, double>(lane, S3, false, V1, V0, V2, true);      // c - Phi^T Q^-1 u
+#pragma unroll 1
+      for (int e = lane; e < nn; e += 32) Ko[(size_t)i * nn + e] = r_from<R>(S5[e] * it);
     } else {
-      double KNi[nn];
-      ok = spd_inverse_full<n>(P.KN, KNi) && ok;
-      for (int e = 0; e < nn; ++e) blk[e] = (carry_d[e] + KNi[e]) * it;
-      for (int a = 0; a < n; ++a) {
-        double s = carry_b[a];
-        for (int c = 0; c < n; ++c) s = fma(KNi[a * n + c], P.muN[c], s);
-        bv[a] = s * it;
-      }
+#pragma unroll 1
+      for (int e = lane; e < nn; e += 32) S1[e] = P.KN[e];
+      if (lane < n) V1[lane] = P.muN[lane];
+      crw::winv<n, double>(lane, S1, row, col, ldd, ok);
+#pragma unroll 1
+      for (int e = lane; e < nn; e += 32) S4[e] = S0[e] + S1[e];
+      crw::mv<n, double>(lane, S1, false, V1, V0, V2, false);     // c + K_N^-1 mu_N
     }
-    for (int r = 0; r < n; ++r)
-      for (int c = 0; c < r; ++c) {
-        double s = 0.5 * (blk[r * n + c] + blk[c * n + r]);
-        blk[r * n + c] = s;
-        blk[c * n + r] = s;
-      }
-    st_blk_from_double<n, R>(Kd + (size_t)i * nn, blk);
-    for (int a = 0; a < n; ++a) b[(size_t)i * n + a] = r_from<R>(bv[a]);
+    __syncwarp();
+#pragma unroll 1
+    for (int e = lane; e < nn; e += 32) {
+      const int a = e / n, c = e - a * n;
+      Kd[(size_t)i * nn + e] = r_from<R>((a == c ? S4[e] : 0.5 * (S4[e] + S4[c * n + a])) * it);
+    }
+    if (lane < n) b[(size_t)i * n + lane] = r_from<R>(V2[lane] * it);
+    __syncwarp();
   }
   ok = __syncthreads_and(ok);
   if (threadIdx.x == 0) {
     P.scal[S_THIGH] = (P.inv_temp_high > 0.0 && it == P.inv_temp_high) ? 1.0 : 0.0;
-    if (ok) ok = bt_solve<n, R>(P, Kd, Ko, b, rp<R>(P.mubar));
     if (!ok) P.scal[S_STATUS] = 1.0;
+  }
+}
+
+// mu_bar = K b (the prior mean) for the K^-1 and b just assembled, by the
+// warp-cooperative block solve; a non-positive pivot marks the prior failed.
+template <int n, typename R>
+__global__ void __launch_bounds__(kCrMaxThreads) k_prior_solve_cta(const PlanDesc* __restrict__ descs, int count) {
+  extern __shared__ __align__(16) unsigned char cr_dyn[];
+  if ((int)blockIdx.x >= count) return;
+  const PlanDesc& P = descs[blockIdx.x];
+  if (P.scal[S_STATUS] != 0.0) return;
+  const bool ok = crw::solve<n, R>(P, rp<R>(P.Kd), rp<R>(P.Ko), rp<R>(P.b), rp<R>(P.mubar),
+                                   reinterpret_cast<R*>(cr_dyn));
+  if (!ok && threadIdx.x == 0) P.scal[S_STATUS] = 1.0;
+}
+
+// After a relinearisation (block form of k_relinearised): the prior cost
+// 1/2 [tr(K^-1 Sigma) + (mu - mu_bar)^T K^-1 (mu - mu_bar)] of the current
+// iterate under the new prior, summed over the block, and a fresh
+// inner-iteration counter.
+template <int n, typename R>
+__global__ void __launch_bounds__(kCrMaxThreads) k_relinearised_cta(const PlanDesc* __restrict__ descs, int count) {
+  constexpr int nn = n * n;
+  __shared__ double red[(kCrMaxThreads / 32) * 4];
+  if ((int)blockIdx.x >= count) return;
+  const PlanDesc& P = descs[blockIdx.x];
+  if (P.scal[S_STATUS] != 0.0) return;
+  const int N = P.N, s = (int)P.scal[S_CUR];
+  const R* Kd = rp<R>(P.Kd);
+  const R* Ko = rp<R>(P.Ko);
+  const R* mu = rp<R>(P.mu[s]);
+  const R* mubar = rp<R>(P.mubar);
+  const R* Sd = rp<R>(P.Sd[s]);
+  const R* So = rp<R>(P.So[s]);
+  R tr = r_fromf<R>(0.0f), qd = r_fromf<R>(0.0f);
+  for (int i = threadIdx.x; i <= N; i += blockDim.x) {
+    R di[n], dn[n];
+    for (int a = 0; a < n; ++a) di[a] = mu[(size_t)i * n + a] - mubar[(size_t)i * n + a];
+    for (int e = 0; e < nn; ++e) tr = r_fma(Kd[(size_t)i * nn + e], Sd[(size_t)i * nn + e], tr);
+    for (int a = 0; a < n; ++a)
+      for (int c = 0; c < n; ++c) qd = r_fma(di[a] * Kd[(size_t)i * nn + a * n + c], di[c], qd);
+    if (i < N) {
+      for (int a = 0; a < n; ++a) dn[a] = mu[(size_t)(i + 1) * n + a] - mubar[(size_t)(i + 1) * n + a];
+      for (int e = 0; e < nn; ++e) {
+        const R E = Ko[(size_t)i * nn + e];
+        tr = r_fma(E + E, So[(size_t)i * nn + e], tr);
+      }
+      for (int a = 0; a < n; ++a)
+        for (int c = 0; c < n; ++c) qd = r_fma((dn[a] + dn[a]) * Ko[(size_t)i * nn + a * n + c], di[c], qd);
+    }
+  }
+  double part[1] = {r_to(tr + qd)};
+  block_sum<1>(part, red);
+  if (threadIdx.x == 0) {
+    P.scal[S_PRIOR] = 0.5 * part[0];
+    P.scal[S_KIN] = 0.0;
+  }
+}
+
+// Results in buffer set 0 and in FP64 (block form of k_finalize), element-
+// parallel: the copy of the current set into set 0, then for double-float
+// the in-place conversion of each element to double (the same thread owns
+// element e in both loops).
+template <int n, typename R>
+__global__ void __launch_bounds__(kCrMaxThreads) k_finalize_cta(const PlanDesc* __restrict__ descs, int count) {
+  if ((int)blockIdx.x >= count) return;
+  const PlanDesc& P = descs[blockIdx.x];
+  const int cur = (int)P.scal[S_CUR];
+  const bool fmt0 = (P.scal[S_FMT] == 0.0);
+  const size_t N = P.N;
+  const size_t cnt[5] = {(N + 1) * n, (N + 1) * n * n, N * n * n, (N + 1) * n * n, N * n * n};
+  __syncthreads();   // every thread has read the flags before thread 0 rewrites them
+  if (cur != 0 && fmt0) {
+    R* dst[3] = {rp<R>(P.mu[0]), rp<R>(P.Sd[0]), rp<R>(P.So[0])};
+    const R* src[3] = {rp<R>(P.mu[cur]), rp<R>(P.Sd[cur]), rp<R>(P.So[cur])};
+    for (int k = 0; k < 3; ++k)
+      for (size_t e = threadIdx.x; e < cnt[k]; e += blockDim.x) dst[k][e] = src[k][e];
+  }
+  if (!std::is_same<R, double>::value && fmt0) {
+    double* bufs[5] = {P.mu[0], P.Sd[0], P.So[0], P.Ld, P.Lo};
+    for (int k = 0; k < 5; ++k) {
+      R* rbuf = rp<R>(bufs[k]);
+      for (size_t e = threadIdx.x; e < cnt[k]; e += blockDim.x) {
+        const double v = r_to(rbuf[e]);
+        bufs[k][e] = v;
+      }
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (cur != 0 && fmt0) P.scal[S_CUR] = 0.0;
+    if (!std::is_same<R, double>::value && fmt0) P.scal[S_FMT] = 1.0;
+  }
+}
+
+// Back to the working format (block form of k_working): double-float
+// results converted in place from FP64, element-parallel.
+template <int n, typename R>
+__global__ void __launch_bounds__(kCrMaxThreads) k_working_cta(const PlanDesc* __restrict__ descs, int count) {
+  if ((int)blockIdx.x >= count) return;
+  const PlanDesc& P = descs[blockIdx.x];
+  const bool fmt1 = (P.scal[S_FMT] == 1.0);
+  __syncthreads();
+  if (!std::is_same<R, double>::value && fmt1) {
+    const size_t N = P.N;
+    double* bufs[5] = {P.mu[0], P.Sd[0], P.So[0], P.Ld, P.Lo};
+    const size_t cnt[5] = {(N + 1) * n, (N + 1) * n * n, N * n * n, (N + 1) * n * n, N * n * n};
+    for (int k = 0; k < 5; ++k) {
+      R* rbuf = rp<R>(bufs[k]);
+      for (size_t e = threadIdx.x; e < cnt[k]; e += blockDim.x) {
+        const R v = r_from<R>(bufs[k][e]);
+        rbuf[e] = v;
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) P.scal[S_FMT] = 0.0;
   }
 }
 
@@ -945,22 +1068,54 @@ __global__ void __launch_bounds__(kCrMaxThreads) k_prior_ltv_cta(const PlanDesc*
 template <int n, typename QT, typename R>
 cudaError_t launch_iter_cta(const Launch& L, int iters, int tpb) {
   if (tpb < 32 || tpb > kCrMaxThreads || (tpb & 31)) return cudaErrorInvalidValue;
-  k_iterate_cta<n, QT, R><<<L.count, tpb, 0, L.stream>>>(L.descs, L.count, iters);
+  const size_t smem = cr_dyn_smem<n, R>(tpb);
+  if (smem > 48 * 1024) {
+    const cudaError_t e = cudaFuncSetAttribute(k_iterate_cta<n, QT, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  k_iterate_cta<n, QT, R><<<L.count, tpb, smem, L.stream>>>(L.descs, L.count, iters);
   return cudaGetLastError();
 }
 
-// Initial iterate, the SLR linearisation (`arg_i` = mode) and the LTV prior,
-// block form, recursions in R (FP64 or double-float).
+// The prior (`arg_i` = its mode), initial iterate, SLR linearisation
+// (`arg_i` = mode), post-relinearisation prior cost, finalisation and return
+// to the working format, block form, recursions in R (FP64 or double-float).
 template <int n, typename R>
 cudaError_t launch_aux_cta(const Launch& L, int phase, int arg_i, int qt32, int tpb) {
   if (tpb < 32 || tpb > kCrMaxThreads || (tpb & 31)) return cudaErrorInvalidValue;
   switch (phase) {
-    case PH_INIT: k_init_cta<n, R><<<L.count, tpb, 0, L.stream>>>(L.descs, L.count); break;
+    case PH_INIT: {
+      const size_t smem = cr_dyn_smem<n, R>(tpb);
+      if (smem > 48 * 1024) {
+        const cudaError_t e =
+            cudaFuncSetAttribute(k_init_cta<n, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+      }
+      k_init_cta<n, R><<<L.count, tpb, smem, L.stream>>>(L.descs, L.count);
+      break;
+    }
     case PH_SLR:
       if (qt32) k_slr_cta<n, float, R><<<L.count, tpb, 0, L.stream>>>(L.descs, L.count, arg_i);
       else k_slr_cta<n, double, R><<<L.count, tpb, 0, L.stream>>>(L.descs, L.count, arg_i);
       break;
-    case PH_PRIOR: k_prior_ltv_cta<n, R><<<L.count, tpb, 0, L.stream>>>(L.descs, L.count); break;
+    case PH_PRIOR: {
+      const size_t smem = (size_t)(tpb / 32) * crw::Lay<n>::ws * sizeof(R);
+      if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k_prior_cta<n, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess)
+          e = cudaFuncSetAttribute(k_prior_solve_cta<n, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+      }
+      k_prior_cta<n, R><<<L.count, tpb, smem, L.stream>>>(L.descs, L.count, arg_i);
+      const cudaError_t e0 = cudaGetLastError();
+      if (e0 != cudaSuccess) return e0;
+      k_prior_solve_cta<n, R><<<L.count, tpb, smem, L.stream>>>(L.descs, L.count);
+      break;
+    }
+    case PH_RELIN: k_relinearised_cta<n, R><<<L.count, tpb, 0, L.stream>>>(L.descs, L.count); break;
+    case PH_FINALIZE: k_finalize_cta<n, R><<<L.count, tpb, 0, L.stream>>>(L.descs, L.count); break;
+    case PH_WORKING: k_working_cta<n, R><<<L.count, tpb, 0, L.stream>>>(L.descs, L.count); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

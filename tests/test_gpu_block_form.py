@@ -154,3 +154,51 @@ def test_double_float_block_form_equals_alone_in_a_batch(pg):
         alone = gpu_solve([pbs[i]], [ops[i]], MIXED_DF)[0]
         np.testing.assert_array_equal(together[i].mu, alone.mu)
         np.testing.assert_array_equal(together[i].Sd, alone.Sd)
+
+
+# ---- the warp-cooperative reduction (n >= 6: one warp per elimination)
+
+@pytest.mark.parametrize("N", [1, 2, 3, 8, 9, 31, 32, 33, 100])
+@pytest.mark.parametrize("tpb", [32, 256])
+def test_warp_reduction_levels_point3d_fp64(pg, N, tpb):
+    """n = 6 over every level structure of the reduction, with a binding KL
+    bound (several trials an iteration), one warp and eight."""
+    pb, op = W.point3d(request=2, N=N)
+    op = replace(op, iters=4, kl_eps=0.05 * (N + 1))
+    res = gpu_solve([pb], [block(op, tpb)], FP64)[0]
+    tol = fp64_tol_from_conditioning(pb)
+    compare_plan(pb, op, res, rtol_mu=tol, rtol_sigma=tol, max_replays=0)
+
+
+@pytest.mark.parametrize("N", [1, 2, 7, 8, 9, 33])
+@pytest.mark.parametrize("prec", [FP64, MIXED_DF])
+def test_warp_reduction_levels_arm(pg, N, prec):
+    """n = 14 (a 7-DOF arm) over level structures of the reduction."""
+    pb, op = W.c3_arm(N=N, iters=4)
+    res = gpu_solve([pb], [block(op, 128)], prec)[0]
+    if prec == FP64:
+        tol = max(TOL_FP64_SMALL["mu"], fp64_tol_from_conditioning(pb))
+        compare_plan(pb, op, res, rtol_mu=tol, rtol_sigma=tol, max_replays=0)
+    else:
+        compare_plan(pb, op, res, rtol_mu=TOL_MIXED["mu"], rtol_sigma=TOL_MIXED["sigma"], prec=prec)
+
+
+def test_c3_arm_full_size_block_form_double_float(pg):
+    """The full-size arm plan (N = 200, 25 iterations) with double-float
+    recursions, the form a single arm plan is served in for latency."""
+    pb, op = W.c3_arm()
+    res = gpu_solve([pb], [block(op, 256)], MIXED_DF)[0]
+    compare_plan(pb, op, res, rtol_mu=TOL_MIXED["mu"], rtol_sigma=TOL_MIXED["sigma"], prec=MIXED_DF)
+
+
+def test_warp_reduction_batch_equals_alone(pg):
+    """Plans of different horizons in one launch give the results they give alone."""
+    probs = [W.point3d(request=r, N=N) for r, N in enumerate([9, 40, 1, 33])]
+    pbs = [p for p, _ in probs]
+    ops = [block(replace(o, iters=5), 64) for _, o in probs]
+    for prec in (FP64, MIXED_DF):
+        together = gpu_solve(pbs, ops, prec)
+        for i in range(len(pbs)):
+            alone = gpu_solve([pbs[i]], [ops[i]], prec)[0]
+            np.testing.assert_array_equal(together[i].mu, alone.mu)
+            np.testing.assert_array_equal(together[i].Sd, alone.Sd)
