@@ -191,6 +191,15 @@ class ClockSampler:
 
 # ---------------------------------------------------------------- CPU baseline
 
+# Iterations of the element-wise sample check.  The dense-horizon plans are
+# ill-conditioned: the oracle against itself, with the goal moved by a relative
+# 1e-12, differs in the marginal covariances by up to 4.2e-5 after one
+# iteration and 7.2e-3 after two (16 sampled plans), so only the first
+# iteration is compared element-wise; the whole plan is checked through
+# invariants that hold at any size.
+SAMPLE_ITERS = 1
+
+
 def _oracle_one(args):
     idx, = args
     sys.path.insert(0, ROOT)
@@ -201,23 +210,86 @@ def _oracle_one(args):
     return time.perf_counter() - t
 
 
-def cpu_baseline(workers: int | None = None, plans_per_worker: int = 1):
+def _oracle_sample(args):
+    """The first SAMPLE_ITERS iterations of plan `idx` (for the sample check),
+    and how far they move when the goal moves by a relative 1e-12."""
+    idx, = args
+    sys.path.insert(0, ROOT)
+    from dataclasses import replace
+
+    import numpy as np
+
+    import oracle
+    pb, op = plan_problem(idx)
+    op1 = replace(op, iters=SAMPLE_ITERS)
+    s = oracle.plan(pb, op1)
+    t = oracle.plan(replace(pb, muN=pb.muN * (1 + 1e-12)), op1)   # the problem's own sensitivity
+    dmu = float(np.linalg.norm(s.mu - t.mu) / np.linalg.norm(s.mu))
+    dsig = float(np.max(np.linalg.norm(s.Sd - t.Sd, axis=(1, 2)) / np.linalg.norm(s.Sd, axis=(1, 2))))
+    return idx, s.mu, s.Sd, [l["beta"] for l in s.logs], dmu, dsig
+
+
+def cpu_baseline(workers: int | None = None, plans_per_worker: int = 1, samples: bool = False):
     """The FP64 oracle on the host cores, one plan per process (spawned), on
-    a bounded sample of the workload: `workers` full plans."""
+    a bounded sample of the workload: `workers` full plans.  With `samples`,
+    afterwards and untimed, the first iterations of the same plans for the
+    sample check."""
     import multiprocessing as mp
     import oracle
     oracle.build()
     workers = workers or max(1, min(os.cpu_count() or 1, 16))
     ctx = mp.get_context("spawn")
     n_plans = workers * plans_per_worker
-    t0 = time.perf_counter()
     with ctx.Pool(workers) as pool:
+        t0 = time.perf_counter()
         times = pool.map(_oracle_one, [(i,) for i in range(n_plans)])
-    wall = time.perf_counter() - t0
-    return {"value": n_plans / wall, "unit": "plans/s", "cores": workers, "kind": "oracle",
-            "sample": f"{n_plans} full plans of the batch workload (one per spawned process), "
-                      f"median {statistics.median(times):.1f} s per plan single-threaded",
-            "wall_s": wall}
+        wall = time.perf_counter() - t0
+        outs = pool.map(_oracle_sample, [(i,) for i in range(n_plans)]) if samples else None
+    res = {"value": n_plans / wall, "unit": "plans/s", "cores": workers, "kind": "oracle",
+           "sample": f"{n_plans} full plans of the batch workload (one per spawned process), "
+                     f"median {statistics.median(times):.1f} s per plan single-threaded",
+           "wall_s": wall}
+    return res, outs
+
+
+def sample_check(samples, precision):
+    """The sampled plans of the batch (the oracle's CPU-baseline plans),
+    SAMPLE_ITERS iterations on the GPU in the batch's precision and form,
+    against the oracle element by element: relative 2-norm of mu over the
+    trajectory, largest relative Frobenius error of a Sigma_ii block, and the
+    step sizes."""
+    from dataclasses import replace
+
+    import numpy as np
+    import torch
+
+    from paper_2411_03416_b300 import _lib as L
+    idx = [i for i, *_ in samples]
+    pairs = [plan_problem(i) for i in idx]
+    probs = [p for p, _ in pairs]
+    opts = [replace(o, iters=SAMPLE_ITERS) for _, o in pairs]
+    st = torch.cuda.Stream()
+    b = L.Batch(probs, opts, precision)
+    b.upload(st.cuda_stream)
+    b.reset(st.cuda_stream)
+    b.run(0, st.cuda_stream)
+    b.download_results(st.cuda_stream)
+    torch.cuda.synchronize()
+    tol_mu, tol_sigma = (1e-9, 1e-9) if precision == 0 else (1e-4, 1e-3)
+    emu, esig, dmu, dsig, same_beta, ok = 0.0, 0.0, 0.0, 0.0, 0, True
+    for k, (_, mu, Sd, betas, smu, ssig) in enumerate(samples):
+        r = b.result(k, full=False)
+        e1 = float(np.linalg.norm(r.mu - mu) / np.linalg.norm(mu))
+        e2 = float(np.max(np.linalg.norm(r.Sd - Sd, axis=(1, 2)) / np.linalg.norm(Sd, axis=(1, 2))))
+        # a plan passes within the tolerance, or within 10x the oracle's own
+        # divergence under a relative 1e-12 change of the goal
+        ok = ok and e1 <= max(tol_mu, 10 * smu) and e2 <= max(tol_sigma, 10 * ssig)
+        emu, esig, dmu, dsig = max(emu, e1), max(esig, e2), max(dmu, smu), max(dsig, ssig)
+        same_beta += int([l["beta"] for l in r.logs] == betas)
+    b.close()
+    return {"plans": len(samples), "iterations": SAMPLE_ITERS, "max_rel_mu": emu, "max_rel_sigma": esig,
+            "same_step_sizes": same_beta, "tol_mu": tol_mu, "tol_sigma": tol_sigma,
+            "oracle_self_divergence": {"mu": dmu, "sigma": dsig}, "pass": ok}
 
 
 # ------------------------------------------------------------------------ main
@@ -266,7 +338,7 @@ def run_reference(args):
         cpu_baseline(cores)
     vals = []
     for _ in range(args.steps):
-        vals.append(cpu_baseline(cores))
+        vals.append(cpu_baseline(cores)[0])
     v = statistics.median(x["value"] for x in vals)
     ms = 1000.0 * statistics.median(x["wall_s"] for x in vals)
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "plans/s", "n_gpus": args.gpus,
@@ -551,9 +623,9 @@ def main():
         return kernel_only(args)
 
     ws, rank, local = dist_init()
-    cpu = None
+    cpu, samples = None, None
     if rank == 0 and not args.no_cpu_baseline:
-        cpu = cpu_baseline()   # before any CUDA work: the pool is spawned, not forked
+        cpu, samples = cpu_baseline(samples=True)   # before any CUDA work: the pool is spawned, not forked
 
     import numpy as np
     import torch
@@ -626,9 +698,21 @@ def main():
     torch.cuda.synchronize()
     trials = []
     statuses = 0
+    # invariants of every plan of the timed batch: all iterations ran, every
+    # accepted step meets the KL bound and is a dyadic fraction of beta_max
+    incomplete, kl_over, off_grid = 0, 0, 0
     for i in range(args.batch):
         r = bm.result(i, full=False)
         trials.append(sum(l["trials"] for l in r.logs))
+        op = opts[i]
+        incomplete += int(len(r.logs) != op.iters)
+        for l in r.logs:
+            if l["beta"] > 0:
+                kl_over += int(l["kl"] > op.kl_eps * (1 + 1e-12))
+                q = l["beta"] / op.beta_max * 2 ** op.max_bisect
+                off_grid += int(abs(q - round(q)) > 1e-9)
+    invariants = {"plans": args.batch, "incomplete": incomplete, "kl_above_bound": kl_over,
+                  "step_not_dyadic": off_grid, "pass": incomplete == 0 and kl_over == 0 and off_grid == 0}
     state_trials = sum((pb.N + 1) * t for pb, t in zip(probs, trials))
     flops = algorithmic_fp64_flops(probs, trials)
     k_ms = sum(run_ms) / len(run_ms)
@@ -676,6 +760,7 @@ def main():
     e2e_max = max_over_ranks(ws, sum(e2e_ms) / 1000.0)
     e2e_value = args.batch * ws * e2e_steps / e2e_max
     bm.close()
+    check = sample_check(samples, head) if samples else None
 
     # ---- the other forms on the same batch
     others = {}
@@ -710,6 +795,7 @@ def main():
                                        "(1.9% of it)"),
                      "algorithmic_fp64_equivalent_flops": flops},
         "cpu_baseline": cpu,
+        "checks": {"invariants": invariants, "sample_vs_oracle": check},
         "e2e": {"value": e2e_value, "unit": "plans/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "ms_per_step": statistics.median(e2e_ms)},
         "serving": serve,
