@@ -628,7 +628,7 @@ DTYPES = {0: "f64", 1: "f32 quadrature + f64 recursions",
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=2)   # 2 x 38 s timed at the default batch
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--batch", type=int, default=75776,
                     help="plans per GPU (75,776: one wave at 16 warps per SM in the thread form; eight waves of the "
