@@ -18,9 +18,11 @@
  * batches of independent plans (pgvimp_batch_*), single rows of the path for
  * inspection (pgvimp_batch_phase), a continuous-batching server
  * (pgvimp_server_*), and an allocation-free marginals call.  Each plan runs
- * in one of two execution forms chosen by pgvimp_options.plan_threads: one
- * GPU thread per plan (throughput), or one thread block per plan with the
- * block recursions by cyclic reduction over time (latency).
+ * in one of three execution forms chosen by pgvimp_options.plan_threads: one
+ * GPU thread per plan (throughput), sixteen lanes per plan for n = 4
+ * (throughput, one block element per lane), or one thread block per plan with
+ * the block recursions by cyclic reduction over time (latency; one warp per
+ * elimination for n >= 6).
  *
  * General rules for every entry point:
  *  - all functions are extern "C", never throw, never abort and return a
@@ -209,7 +211,7 @@ pgvimp_status pgvimp_batch_reset(pgvimp_batch *b, void *stream);
  * -- factor expectations (Sec. 4.3, 5.2), gradients (eq. gradients_psid),
  * the update of Thm 1 (or NGD, Sec. 3.1(d)) with the KL-bounded step-size
  * search (App. C), marginals of the new precision (Sec. 5.1).  A plan that
- * has not started is first initialised (prior, Alg. 1 lines 1-2).  SLR models
+ * has not started is first initialised (prior and initial iterate, the set-up of Alg. 1).  SLR models
  * relinearise (Sec. 6.2, Alg. 2) at the start of each outer iteration.
  * Asynchronous on `stream`; a plan that fails (prior or marginals not PD)
  * records its status and stops, the others continue. */
@@ -239,7 +241,7 @@ pgvimp_status pgvimp_batch_destroy(pgvimp_batch *b);
  * device code the fused run uses, so that each row can be checked on its own.
  * Buffers are read and written with pgvimp_batch_read / pgvimp_batch_write. */
 typedef enum {
-  PGVIMP_PHASE_PRIOR = 0,     /* Alg. 1, lines 1-2: Phi_i, Q_i (Van Loan), K^-1, b; initial mu, Lambda */
+  PGVIMP_PHASE_PRIOR = 0,     /* the set-up of Alg. 1: Phi_i, Q_i (Van Loan), K^-1, b; initial mu, Lambda */
   PGVIMP_PHASE_MARGINALS = 1, /* Sec. 5.1: Sigma_ii, Sigma_{i+1,i}, log det of the current Lambda */
   PGVIMP_PHASE_QUAD = 2,      /* Sec. 4.1-4.3: E[psi_i] and the gradients g_i, G_i at (mu, Sigma_ii) */
   PGVIMP_PHASE_TRIAL = 3,     /* Thm 1 at step `arg`: mu', Sigma' blocks, log det, KL, feasibility */

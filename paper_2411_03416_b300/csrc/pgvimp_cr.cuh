@@ -823,7 +823,7 @@ __global__ void __launch_bounds__(kCrMaxThreads) k_slr_cta(const PlanDesc* __res
   if (!ok && threadIdx.x == 0) P.scal[S_STATUS] = 4.0;
 }
 
-// The GP prior (Sec. 3, Alg. 1 line 1; for mode 1 the SLR linearisation's
+// The GP prior (Sec. 3; the prior step of Alg. 1; for mode 1 the SLR linearisation's
 // LTV prior of Alg. 2) with its work spread over the block.  First the Van
 // Loan factors Phi_i, Q_i, u_i, one thread per step (a single step for a
 // time-invariant system), stored to the per-step scratch with scalar stores.

@@ -1,7 +1,7 @@
 // pgvimp_kernels.cuh -- the P-GVIMP hot path on sm_103a, one plan per thread.
 //
 // Rows of the path and where they live:
-//   prior build (Alg. 1, lines 1-2)          prior_build<n, R>        / k_prior
+//   prior build (Alg. 1, its set-up)         prior_build<n, R>        / k_prior
 //   marginals on the chain (Sec. 5.1)        marginals<n, R>          / k_init, k_marginals
 //   factor expectations (Sec. 4.1-4.3)       quad_factor<n, QT, R>    / k_quad, k_iterate
 //   gradient assembly (Sec. 4.2)             quad_factor<n, QT, R>
