@@ -91,11 +91,11 @@ typedef enum { PGVIMP_UPDATE_PROX = 0, PGVIMP_UPDATE_NGD = 1 } pgvimp_update;
  * MIXED_DF: as MIXED, but the recursions run in double-float arithmetic
  * (pairs of FP32 values, ~48-bit significand) on the FP32 pipe, which on B300
  * issues at 64x the FP64 rate; results are returned in FP64.  Its errors
- * follow its ~2^-48 unit roundoff: on precision matrices conditioned near
- * 1e12 (dense 750-step horizons through clutter) the marginal covariances
- * after one iteration were 3e-3 to 6e-3 from the FP64 oracle, against 1e-4
- * with MIXED, so MIXED is the form whose stated error bounds hold on every
- * input.  The single-row phases (pgvimp_batch_phase other than PRIOR) need
+ * follow its ~2^-48 unit roundoff: on precision matrices conditioned at
+ * 6e11 to 4e12 (dense 750-step horizons through clutter) the marginal
+ * covariances after one iteration were 1e-3 to 6e-3 from the FP64 oracle,
+ * against 1e-4 with MIXED, so MIXED is the form whose stated error bounds
+ * hold on every input.  The single-row phases (pgvimp_batch_phase other than PRIOR) need
  * PLAIN_FP64 or MIXED. */
 typedef enum { PGVIMP_PREC_PLAIN_FP64 = 0, PGVIMP_PREC_MIXED = 1, PGVIMP_PREC_MIXED_DF = 2 } pgvimp_precision;
 
