@@ -95,8 +95,8 @@ typedef enum { PGVIMP_UPDATE_PROX = 0, PGVIMP_UPDATE_NGD = 1 } pgvimp_update;
  * 6e11 to 4e12 (dense 750-step horizons through clutter) the marginal
  * covariances after one iteration were 1e-3 to 6e-3 from the FP64 oracle,
  * against 1e-4 with MIXED, so MIXED is the form whose stated error bounds
- * hold on every input.  The single-row phases (pgvimp_batch_phase other than PRIOR) need
- * PLAIN_FP64 or MIXED. */
+ * hold on every input.  The single-row phases (pgvimp_batch_phase other
+ * than PRIOR) need PLAIN_FP64 or MIXED. */
 typedef enum { PGVIMP_PREC_PLAIN_FP64 = 0, PGVIMP_PREC_MIXED = 1, PGVIMP_PREC_MIXED_DF = 2 } pgvimp_precision;
 
 /* One planning problem.  All pointers are host pointers, row-major FP64
